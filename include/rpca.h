@@ -1,0 +1,164 @@
+/*
+ * rpca.h - C ABI of the GB300 (sm_103a) randomized PCA library (librpca.so).
+ *
+ * The method is the randomized range finder with power iterations of
+ * Szlam, Kluger & Tygert, "An implementation of a randomized algorithm for
+ * principal component analysis" (2014):
+ *
+ *   Y = A_c Omega                      (Section 2; Omega n x l i.i.d. N(0,1))
+ *   its times: Q = renorm(Y); X = A_c^* Q; Q = renorm(X); Y = A_c Q
+ *                                      (Section 2 power iterations; Section 5
+ *                                       renormalises after every product)
+ *   Q = orthonormal basis of range(Y)  (Section 5: QR at the last step)
+ *   B = Q^* A_c; W Sigma V^* = B; U = Q W   (Eqs. i2, i3, i4)
+ *
+ * where A_c = A - 1 c (c = column means, Section 5's implicit centring) unless
+ * `raw` is set, in which case A_c = A.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are FP32, row-major, with an explicit leading dimension
+ *    (elements between consecutive rows).  A is m x n with lda >= n.
+ *  - Every pointer is caller-owned memory; device pointers unless stated.
+ *    The library never allocates on the compute path: the caller sizes a
+ *    workspace with the matching *_workspace_size query and passes it in.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t).  The return value
+ *    reports errors found on the host (arguments, launch failures).  Errors
+ *    found on the device (non-finite input, numerical breakdown, timeouts)
+ *    are written to a status word inside the workspace; read it with
+ *    rpca_read_status after the work has run.
+ *  - Return codes: 0 = success, >0 = success with a note (RPCA_FELL_BACK),
+ *    <0 = error (see rpca_status).  rpca_status_string names each.
+ *  - Inputs are never modified.  Outputs are fully written on success.
+ */
+#ifndef RPCA_H
+#define RPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t; declared here so that users need no CUDA headers. */
+struct CUstream_st;
+typedef struct CUstream_st *rpca_stream_t;
+
+typedef enum rpca_status {
+    RPCA_OK = 0,
+    RPCA_FELL_BACK = 1,          /* succeeded on a fallback (shifted CholeskyQR, plain sketch) */
+    RPCA_ERR_INVALID_ARG = -1,   /* k < 1, l < k, l > min(m, n), l > RPCA_MAX_L, its < 0, null, lda < n ... */
+    RPCA_ERR_WORKSPACE = -2,     /* workspace null, too small, or misaligned (needs 256-byte alignment) */
+    RPCA_ERR_CUDA = -3,          /* a kernel launch or CUDA runtime call failed */
+    RPCA_ERR_NONFINITE = -4,     /* NaN or Inf reached a Gram matrix (input A not finite) */
+    RPCA_ERR_BREAKDOWN = -5,     /* a factorisation failed even after its fallback */
+    RPCA_ERR_TIMEOUT = -6,       /* a bounded device-side wait expired */
+    RPCA_ERR_UNSUPPORTED = -7    /* option combination not built (e.g. precision on this shape) */
+} rpca_status;
+
+/* Largest sketch width l (the l x l factors live in one CTA's shared memory). */
+#define RPCA_MAX_L 224
+
+typedef enum rpca_precision {
+    RPCA_PREC_FP32 = 0,          /* passes over A in FP32 FFMA (the plain form) */
+    RPCA_PREC_BF16X3 = 1         /* passes over A on tcgen05 tensor cores: a = a_hi + a_lo
+                                    in BF16, three products accumulated in FP32 (TMEM) */
+} rpca_precision;
+
+typedef enum rpca_renorm {
+    RPCA_RENORM_CHOLQR = 0,      /* Gram + Cholesky renormalisation (span-equivalent to LU) */
+    RPCA_RENORM_LU = 1           /* tall-skinny LU with tournament pivoting (Section 5's lu) */
+} rpca_renorm;
+
+typedef struct rpca_opts {
+    int32_t k;                   /* rank of the returned approximation, 1 <= k <= l */
+    int32_t l;                   /* sketch width, k <= l <= min(m, n); paper default k + 2 */
+    int32_t its;                 /* power iterations, >= 0; paper default 2 */
+    int32_t raw;                 /* nonzero: approximate A itself, no column centring */
+    uint64_t seed;               /* Philox key for Omega (stream 0) */
+    int32_t precision;           /* rpca_precision */
+    int32_t renorm;              /* rpca_renorm, for every renormalisation but the last */
+    const float *omega;          /* optional caller-supplied Omega (n x l, row-major,
+                                    leading dimension l, device); NULL = Philox */
+    const float *col_weights;    /* optional d (n, device): the sketch uses diag(d) Omega;
+                                    NULL = plain Gaussian sketch */
+} rpca_opts;
+
+/* Fill `o` with the paper's defaults for rank k: l = k + 2, its = 2,
+ * raw = 0, seed = 0, FP32, CholeskyQR, no caller Omega, no weights. */
+void rpca_default_opts(rpca_opts *o, int32_t k);
+
+/* ------------------------------------------------------------------------
+ * Dense randomized PCA (Sections 2 and 5; Eqs. i1-i4).
+ *
+ * A      : m x n FP32, row-major, leading dimension lda >= n (device).
+ * U      : m x k output, leading dimension ldu >= k (device).
+ * S      : k outputs, descending (device).
+ * V      : n x k output, leading dimension ldv >= k (device).
+ * ws     : workspace of ws_bytes >= rpca_dense_workspace_size(m, n, o),
+ *          256-byte aligned (device).  Holds the status word.
+ * A_c ~ U diag(S) V^T.  Signs: each column of V has its largest-magnitude
+ * entry positive, and the matching column of U is flipped with it.
+ * ---------------------------------------------------------------------- */
+size_t rpca_dense_workspace_size(int64_t m, int64_t n, const rpca_opts *o);
+int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, const rpca_opts *o,
+               float *U, int64_t ldu, float *S, float *V, int64_t ldv,
+               void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Sparse randomized PCA: the same method with A in CSR form (Section 5 notes
+ * that the same code serves dense and sparse A).
+ *
+ * row_ptr: m + 1 int32 (device), row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz.
+ * col_idx: nnz int32 in [0, n) (device).  val: nnz FP32 (device).
+ * Duplicate column indices within a row are summed.
+ * Other arguments as rpca_dense.
+ * ---------------------------------------------------------------------- */
+size_t rpca_csr_workspace_size(int64_t m, int64_t n, int64_t nnz, const rpca_opts *o);
+int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+             const float *val, const rpca_opts *o, float *U, int64_t ldu, float *S,
+             float *V, int64_t ldv, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Spectral-norm residual estimate ||A_c - U diag(S) V^T||_2 by the power
+ * method from a random start (Section 4).
+ *
+ * x0 = N(0,1) n-vector from Philox key (seed, 1), normalised; each of `iters`
+ * iterations forms z = E^T (E x), lambda = |z|, x = z / |z|; the estimate
+ * is sqrt(lambda) (never above the true norm).  U, S, V as returned by
+ * rpca_dense (k columns).  The estimate (FP64) is written to est (device).
+ * ---------------------------------------------------------------------- */
+size_t rpca_resid_workspace_size(int64_t m, int64_t n, int32_t k);
+int rpca_resid_norm(const float *A, int64_t m, int64_t n, int64_t lda, int32_t raw,
+                    const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv,
+                    int32_t k, int32_t iters, uint64_t seed, double *est,
+                    void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * The sketch's test matrix alone (Section 2; the step every call starts with).
+ * Writes Omega (n x l, row-major, leading dimension ldo >= l, device): entry
+ * (i, j) is element e = i*l + j of the stream in which Philox4x64-10 block b
+ * (counter (b, 0, 0, 0), key (seed, stream_id)) gives words w0..w3, mapped to
+ * u = ((w >> 41) + 1/2) / 2^23 and by Box-Muller to elements 4b..4b+3.
+ * ---------------------------------------------------------------------- */
+int rpca_gaussian_omega(int64_t n, int32_t l, uint64_t seed, uint64_t stream_id,
+                        float *omega, int64_t ldo, rpca_stream_t stream);
+
+/* Raw Philox4x64-10 words: out[4 b + w] = word w of block (counter (first + b, 0, 0, 0),
+ * key (key0, key1)) for b < nblocks (device output). */
+int rpca_philox4x64_10(uint64_t key0, uint64_t key1, uint64_t first, int64_t nblocks,
+                       uint64_t *out, rpca_stream_t stream);
+
+/* Wait for `stream`, then copy the device status word out of `ws` into *status. */
+int rpca_read_status(const void *ws, rpca_stream_t stream, int32_t *status);
+
+/* Name of a status code. */
+const char *rpca_status_string(int status);
+
+/* Number of kernels this library has launched in this process. */
+int64_t rpca_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPCA_H */

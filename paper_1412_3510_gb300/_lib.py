@@ -1,0 +1,81 @@
+"""ctypes loader for librpca.so (declarations mirror include/rpca.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librpca.so")
+
+RPCA_OK = 0
+RPCA_FELL_BACK = 1
+RPCA_ERR_INVALID_ARG = -1
+RPCA_ERR_WORKSPACE = -2
+RPCA_ERR_CUDA = -3
+RPCA_ERR_NONFINITE = -4
+RPCA_ERR_BREAKDOWN = -5
+RPCA_ERR_TIMEOUT = -6
+RPCA_ERR_UNSUPPORTED = -7
+RPCA_MAX_L = 224
+
+PREC = {"fp32": 0, "bf16x3": 1}
+RENORM = {"cholqr": 0, "lu": 1}
+
+
+class RpcaOpts(C.Structure):
+    _fields_ = [
+        ("k", C.c_int32), ("l", C.c_int32), ("its", C.c_int32), ("raw", C.c_int32),
+        ("seed", C.c_uint64), ("precision", C.c_int32), ("renorm", C.c_int32),
+        ("omega", C.c_void_p), ("col_weights", C.c_void_p),
+    ]
+
+
+# (name, restype, argtypes) for every symbol include/rpca.h declares
+_I64, _I32, _U64, _P, _SZ = C.c_int64, C.c_int32, C.c_uint64, C.c_void_p, C.c_size_t
+_OPTS = C.POINTER(RpcaOpts)
+SIGNATURES = [
+    ("rpca_default_opts", None, [_OPTS, _I32]),
+    ("rpca_dense_workspace_size", _SZ, [_I64, _I64, _OPTS]),
+    ("rpca_dense", C.c_int, [_P, _I64, _I64, _I64, _OPTS, _P, _I64, _P, _P, _I64, _P, _SZ, _P]),
+    ("rpca_csr_workspace_size", _SZ, [_I64, _I64, _I64, _OPTS]),
+    ("rpca_csr", C.c_int, [_I64, _I64, _I64, _P, _P, _P, _OPTS, _P, _I64, _P, _P, _I64, _P, _SZ, _P]),
+    ("rpca_resid_workspace_size", _SZ, [_I64, _I64, _I32]),
+    ("rpca_resid_norm", C.c_int, [_P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P, _I64, _I32, _I32, _U64,
+                                  _P, _P, _SZ, _P]),
+    ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
+    ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
+    ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
+    ("rpca_status_string", C.c_char_p, [C.c_int]),
+    ("rpca_launch_count", C.c_int64, []),
+]
+
+_lib = None
+
+
+def header_symbols() -> list[str]:
+    """Every function name declared in include/rpca.h (parsed from the header text)."""
+    import re
+    path = os.path.join(os.path.dirname(_HERE), "include", "rpca.h")
+    with open(path) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(rpca_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load librpca.so and declare its signatures; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

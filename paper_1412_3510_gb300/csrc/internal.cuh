@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of librpca.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <algorithm>
+
+#include "rpca.h"
+
+namespace rpca {
+
+// ---------------------------------------------------------------------------
+// device status word (first 256 bytes of every workspace)
+// ---------------------------------------------------------------------------
+struct DevStatus {
+    int32_t status;        // 0, or the most severe (most negative) error code
+    int32_t flags;         // bit 0: fell back (informative)
+    int32_t shifts;        // number of shifted Cholesky factorisations
+    int32_t jacobi_sweeps; // sweeps used by the last small SVD
+    int32_t jacobi_unconverged;
+    int32_t timeouts;
+    int32_t pad[58];
+};
+static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
+
+__device__ __forceinline__ void dev_fail(DevStatus *st, int code) {
+    atomicMin(&st->status, code);
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting
+// ---------------------------------------------------------------------------
+void count_launch();
+int check_launch();   // RPCA_OK or RPCA_ERR_CUDA after a <<<>>> launch
+
+#define RPCA_CHECK_LAUNCH()                                  \
+    do {                                                     \
+        rpca::count_launch();                                \
+        int _e = rpca::check_launch();                       \
+        if (_e != RPCA_OK) return _e;                        \
+    } while (0)
+
+#define RPCA_TRY(expr)                                       \
+    do {                                                     \
+        int _e = (expr);                                     \
+        if (_e < 0) return _e;                               \
+    } while (0)
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Padded sketch width: at least one spare column (the ones column that
+// carries the column sums of A through the adjoint products), multiple of 8.
+static inline int padded_l(int l) { return (int)round_up(l + 1, 8); }
+
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// launchers (each returns an rpca_status)
+// ---------------------------------------------------------------------------
+
+// Omega: n x l Gaussian (optionally scaled by row weights d[i]), written into
+// out (leading dimension ldo).  Columns [l, ldo) are not touched.
+int launch_omega(int64_t n, int l, uint64_t seed, uint64_t stream_id, const float *weights,
+                 float *out, int64_t ldo, cudaStream_t s);
+
+// C[M x N] (ldc) = op(A) B over the K range split into `splits` slices;
+// slice z writes C + z * split_stride.  op(A) = A (A is M x K, lda) when
+// !trans_a, and A^T (A stored K x M, lda) when trans_a.  B is K x N (ldb).
+int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
+                 const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
+                 int64_t split_stride, cudaStream_t s);
+
+// Number of K slices launch_sgemm should use so that the grid fills the GPU.
+int choose_splits(int64_t M, int64_t N, int64_t K);
+
+// Column sums of the first l columns of Y (rows x ld), partial per chunk of
+// rows: part[chunk * l + c].  Returns the number of chunks via *nchunks.
+int launch_colsum_partial(const float *Y, int64_t rows, int l, int64_t ld, float *part,
+                          int *nchunks, cudaStream_t s);
+int colsum_chunks(int64_t rows);
+
+// Y[i][c] -= mean_c for c < l (mean from the partials), Y[i][c] = 0 for l <= c < ld.
+int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, int nchunks,
+                  cudaStream_t s);
+
+// Finish a renormalised tall block: Q[:, l] = ones_value, Q[:, l+1:ld) = 0;
+// when part != NULL also write per-chunk column sums of Q[:, :l].
+int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value, float *part,
+                    cudaStream_t s);
+
+// G (FP64, l x l) = sum over splits of the FP32 partial Grams part[s] (lp x lp).
+int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s);
+
+// X = sum_s part[s] (rows x lp); when centring, X[:, c] -= (X[:, l] / m) * qsum[c]
+// with qsum from the column-sum partials of Q; padding columns zeroed.
+int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, int lp, float *X,
+                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s);
+
+// One CTA: Cholesky G = R^T R in FP32 (shifted on breakdown), Rinv (lp x lp,
+// zero padded) = R^-1; optionally Racc_out = R * Racc_in (l x l, upper).
+int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
+                    float *Racc_out, DevStatus *st, cudaStream_t s);
+
+// Small SVD of R^T (R = Racc, l x l upper): writes Wk (lp x kp, U-side
+// factors, k leading left singular vectors of R^T), sig (l, descending) and
+// Zk (lp x kp, V-side).  rot/zbuf are scratch.
+int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, float *Zk,
+                     float *sig, float *rot, float *zbuf, int *perm, DevStatus *st, cudaStream_t s);
+size_t small_svd_rot_floats(int l);
+
+// Sign convention and singular values: for r < k, flip V[:, r] so that its
+// largest-magnitude entry is positive, scale Wk's column r by the same sign,
+// and write S[r] = sig[r].
+int launch_sign_fix(float *V, int64_t n, int64_t ldv, int k, float *Wk, int lp, int kp,
+                    const float *sig, float *S, cudaStream_t s);
+
+// Residual estimator kernels (power method on E = A_c - U S V^T).
+int launch_fill(float *p, int64_t count, float value, cudaStream_t s);
+
+}  // namespace rpca

@@ -1,0 +1,202 @@
+// The randomized PCA of Szlam, Kluger & Tygert (2014), Sections 2 and 5, as a
+// sequence of launches on one stream:
+//
+//   Omega (Philox)                      Section 2 test vectors
+//   Y = A_c Omega                       the sketch
+//   Q = renorm(Y)                       Section 5: renormalise every product
+//   its times: X = A_c^* Q; Q' = renorm(X); Y = A_c Q'; Q = renorm(Y)
+//   the last renormalisation is a full orthonormalisation (Section 5's QR),
+//   here CholeskyQR applied three times (the first shifted if needed)
+//   B^* = A_c^* Q; B^* = Q2 R (CholeskyQR x3); R^T = W Sigma Z^T (Jacobi)
+//   V = Q2 Z, U = Q W (Eq. i4), first k columns, sign convention on V.
+//
+// Blocks on the m side (Y, Q) and the n side (X, Q') are FP32, row-major with
+// the padded width lp = round_up(l + 1, 8); column l of a Q that enters an
+// adjoint product holds ones (it carries m c through A^T), every other padding
+// column holds zeros.
+#include "pipeline.cuh"
+
+namespace rpca {
+
+namespace {
+
+__global__ void copy_scale_kernel(int64_t n, int l, const float *__restrict__ src, int64_t lds,
+                                  const float *__restrict__ w, float *__restrict__ dst, int64_t ldd) {
+    const int64_t total = n * (int64_t)l;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / l;
+        const int j = (int)(e % l);
+        float v = src[i * lds + j];
+        if (w) v *= w[i];
+        dst[i * ldd + j] = v;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits) {
+    Layout L;
+    L.m = m; L.n = n; L.l = l; L.k = k;
+    L.lp = padded_l(l);
+    L.kp = (int)round_up(k, 4);
+    L.s_adj = adjoint_splits;
+    L.s_gram_m = choose_splits(L.lp, L.lp, m);
+    L.s_gram_n = choose_splits(L.lp, L.lp, n);
+    L.cchunks = colsum_chunks(m);
+    const size_t lp = (size_t)L.lp;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
+    L.status = take(sizeof(DevStatus));
+    L.x0 = take((size_t)n * lp * 4);
+    L.x1 = take((size_t)n * lp * 4);
+    L.y0 = take((size_t)m * lp * 4);
+    L.y1 = take((size_t)m * lp * 4);
+    size_t part = std::max({(size_t)std::max(L.s_adj, 1) * (size_t)n * lp,
+                            (size_t)L.s_gram_m * lp * lp, (size_t)L.s_gram_n * lp * lp});
+    L.part = take(part * 4);
+    L.cpart = take((size_t)L.cchunks * l * 4);
+    L.qpart = take((size_t)L.cchunks * l * 4);
+    L.G = take((size_t)l * l * 8);
+    L.rinv = take(lp * lp * 4);
+    L.racc0 = take((size_t)l * l * 4);
+    L.racc1 = take((size_t)l * l * 4);
+    L.wk = take(lp * L.kp * 4);
+    L.zk = take(lp * L.kp * 4);
+    L.sig = take(lp * 4);
+    L.perm = take(lp * 4);
+    L.rot = take(small_svd_rot_floats(l) * 4);
+    L.zbuf = take(256);
+    L.total = off;
+    return L;
+}
+
+int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64_t ldu,
+                 const float *S, const float *V, int64_t ldv, const void *ws, size_t ws_bytes,
+                 size_t need) {
+    if (!o || !U || !S || !V) return RPCA_ERR_INVALID_ARG;
+    if (m < 1 || n < 1) return RPCA_ERR_INVALID_ARG;
+    if (o->k < 1 || o->l < o->k || o->l > RPCA_MAX_L || (int64_t)o->l > std::min(m, n)) return RPCA_ERR_INVALID_ARG;
+    if (o->its < 0 || o->its > 1000) return RPCA_ERR_INVALID_ARG;
+    if (ldu < o->k || ldv < o->k) return RPCA_ERR_INVALID_ARG;
+    if (o->precision != RPCA_PREC_FP32 && o->precision != RPCA_PREC_BF16X3) return RPCA_ERR_INVALID_ARG;
+    if (o->renorm != RPCA_RENORM_CHOLQR && o->renorm != RPCA_RENORM_LU) return RPCA_ERR_INVALID_ARG;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
+    return RPCA_OK;
+}
+
+namespace {
+
+struct Ctx {
+    const Layout &L;
+    char *ws;
+    cudaStream_t s;
+    DevStatus *st;
+    template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+};
+
+// One CholeskyQR round: out = in R^-1 with G = in^T in = R^T R.
+int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int splits,
+                 const float *racc_in, float *racc_out) {
+    const Layout &L = c.L;
+    const int lp = L.lp;
+    float *part = c.at<float>(L.part);
+    double *G = c.at<double>(L.G);
+    float *rinv = c.at<float>(L.rinv);
+    RPCA_TRY(launch_sgemm(true, lp, lp, rows, in, lp, in, lp, part, lp, splits, (int64_t)lp * lp, c.s));
+    RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s));
+    RPCA_TRY(launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s));
+    RPCA_TRY(launch_sgemm(false, rows, lp, lp, in, lp, rinv, lp, out, lp, 1, 0, c.s));
+    return RPCA_OK;
+}
+
+// m-side renormalisation of y0 (a fresh product A X) into y1.
+int renorm_m(const Ctx &c, bool raw, bool final_) {
+    const Layout &L = c.L;
+    float *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
+    if (!raw) {
+        int nch = 0;
+        RPCA_TRY(launch_colsum_partial(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), &nch, c.s));
+        RPCA_TRY(launch_center(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), nch, c.s));
+    }
+    RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr));
+    if (final_) {
+        RPCA_TRY(cholqr_round(c, y1, y0, L.m, L.s_gram_m, nullptr, nullptr));
+        RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr));
+    }
+    RPCA_TRY(launch_finalize(y1, L.m, L.l, L.lp, raw ? 0.f : 1.f, raw ? nullptr : c.at<float>(L.qpart), c.s));
+    return RPCA_OK;
+}
+
+// n-side renormalisation of x0 (a fresh product A^T Q) into x1; the final one
+// accumulates the triangular factor R = R3 R2 R1 into racc0.
+int renorm_n(const Ctx &c, bool final_) {
+    const Layout &L = c.L;
+    float *x0 = c.at<float>(L.x0), *x1 = c.at<float>(L.x1);
+    float *r0 = c.at<float>(L.racc0), *r1 = c.at<float>(L.racc1);
+    if (!final_) return cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, nullptr);
+    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, r0));
+    RPCA_TRY(cholqr_round(c, x1, x0, L.n, L.s_gram_n, r0, r1));
+    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, r1, r0));
+    return RPCA_OK;
+}
+
+// x0 = A_c^* y1  (Section 5: (Q'*A)' - c'*(ones(1,m)*Q)).
+int adjoint_pass(const Operator &op, const Ctx &c, bool raw) {
+    const Layout &L = c.L;
+    float *part = c.at<float>(L.part);
+    RPCA_TRY(op.adjoint(c.at<float>(L.y1), L.lp, part, c.s));
+    const int splits = op.adjoint_splits(L.lp);
+    RPCA_TRY(launch_adjoint_reduce(part, std::max(splits, 1), L.n, L.l, L.lp, c.at<float>(L.x0), raw ? 0 : 1,
+                                   (double)L.m, c.at<float>(L.qpart), L.cchunks, c.s));
+    return RPCA_OK;
+}
+
+}  // namespace
+
+int run_pipeline(const Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
+                 int64_t ldv, void *ws, const Layout &L, cudaStream_t s) {
+    Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status)};
+    const bool raw = o->raw != 0;
+    const int l = L.l, lp = L.lp;
+    float *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
+
+    if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (cudaMemsetAsync(x1, 0, (size_t)L.n * lp * 4, s) != cudaSuccess) return RPCA_ERR_CUDA;
+
+    // test matrix (Section 2), optionally weighted by d (Omega' = diag(d) Omega)
+    if (o->omega) {
+        const int64_t grid = std::min<int64_t>(cdiv(L.n * (int64_t)l, 256), (int64_t)num_sms() * 8);
+        copy_scale_kernel<<<(unsigned)grid, 256, 0, s>>>(L.n, l, o->omega, l, o->col_weights, x1, lp);
+        RPCA_CHECK_LAUNCH();
+    } else {
+        RPCA_TRY(launch_omega(L.n, l, o->seed, 0, o->col_weights, x1, lp, s));
+    }
+
+    // sketch and power iterations
+    RPCA_TRY(op.apply(x1, lp, y0, s));
+    RPCA_TRY(renorm_m(c, raw, o->its == 0));
+    for (int it = 1; it <= o->its; ++it) {
+        RPCA_TRY(adjoint_pass(op, c, raw));
+        RPCA_TRY(renorm_n(c, false));
+        RPCA_TRY(op.apply(x1, lp, y0, s));
+        RPCA_TRY(renorm_m(c, raw, it == o->its));
+    }
+
+    // B^* = A_c^* Q (Eq. i2), B^* = Q2 R, SVD of R^T (Eq. i3)
+    RPCA_TRY(adjoint_pass(op, c, raw));
+    RPCA_TRY(renorm_n(c, true));
+    float *wk = c.at<float>(L.wk), *zk = c.at<float>(L.zk), *sig = c.at<float>(L.sig);
+    RPCA_TRY(launch_small_svd(c.at<float>(L.racc0), l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
+                              c.at<float>(L.zbuf), c.at<int>(L.perm), c.st, s));
+
+    // V = Q2 Z_k, signs, U = Q W_k (Eq. i4)
+    RPCA_TRY(launch_sgemm(false, L.n, L.k, lp, x1, lp, zk, L.kp, V, ldv, 1, 0, s));
+    RPCA_TRY(launch_sign_fix(V, L.n, ldv, L.k, wk, lp, L.kp, sig, S, s));
+    RPCA_TRY(launch_sgemm(false, L.m, L.k, lp, y1, lp, wk, L.kp, U, ldu, 1, 0, s));
+    return RPCA_OK;
+}
+
+}  // namespace rpca

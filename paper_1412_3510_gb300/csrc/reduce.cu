@@ -1,0 +1,199 @@
+// Column statistics and reductions around the products.
+//
+// Implicit centring (Section 5).  The paper applies the centred matrix as
+// A*Q - ones(m,1)*(c*Q) with c the column means of A.  Since the means of the
+// rows of A*Q are exactly c*Q, the A-side correction is applied here as
+// "subtract from every row of Y = A*X the mean of Y's rows", which needs no
+// separate pass over A.  The adjoint side, (Q'*A)' - c'*(ones(1,m)*Q), needs c
+// itself: it arrives through a column of ones appended to Q (column l of the
+// padded block), whose product with A^T is m c.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace rpca {
+
+namespace {
+
+constexpr int kChunkRows = 512;     // rows per partial column sum
+
+// part[chunk * l + c] = sum of Y[r][c] over the rows r of the chunk (c < l).
+// When write_pad, also set Y[r][l] = ones_value and Y[r][c] = 0 for l < c < ld.
+__global__ void __launch_bounds__(256)
+colsum_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld, float *__restrict__ part,
+              int write_pad, float ones_value) {
+    __shared__ float red[256];
+    const int64_t r0 = (int64_t)blockIdx.x * kChunkRows;
+    const int64_t r1 = min(rows, r0 + kChunkRows);
+    if (write_pad) {
+        const int npad = (int)(ld - l);
+        for (int64_t e = threadIdx.x; e < (r1 - r0) * npad; e += blockDim.x) {
+            const int64_t r = r0 + e / npad;
+            const int c = l + (int)(e % npad);
+            Y[r * ld + c] = (c == l) ? ones_value : 0.f;
+        }
+    }
+    if (!part) return;
+    // threads: column c = t % cw, row group g = t / cw
+    const int cw = min(l, 256);
+    const int groups = 256 / cw;
+    for (int cb = 0; cb < l; cb += cw) {
+        const int t = threadIdx.x;
+        const int c = cb + t % cw;
+        const int g = t / cw;
+        float s = 0.f;
+        if (g < groups && c < l)
+            for (int64_t r = r0 + g; r < r1; r += groups) s += Y[r * ld + c];
+        red[t] = s;
+        __syncthreads();
+        if (t < cw && cb + t < l) {
+            float tot = 0.f;
+            for (int q = 0; q < groups; ++q) tot += red[q * cw + t];
+            part[(int64_t)blockIdx.x * l + cb + t] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Y[r][c] -= mean_c (c < l), Y[r][c] = 0 (l <= c < ld); mean from the partials (FP64 sum).
+__global__ void __launch_bounds__(256)
+center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
+              const float *__restrict__ part, int nchunks) {
+    __shared__ float mu[RPCA_MAX_L];
+    for (int c = threadIdx.x; c < l; c += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nchunks; ++q) s += (double)part[(int64_t)q * l + c];
+        mu[c] = (float)(s / (double)rows);
+    }
+    __syncthreads();
+    const int64_t total = rows * ld;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % ld);
+        Y[e] = (c < l) ? Y[e] - mu[c] : 0.f;
+    }
+}
+
+// G[a][b] = sum_s part[s][a][b] in FP64 (a, b < l).
+__global__ void __launch_bounds__(256)
+gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G) {
+    const int64_t total = (int64_t)l * l;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / l), b = (int)(e % l);
+        double s = 0.0;
+        const float *p = part + (int64_t)a * lp + b;
+        const int64_t stride = (int64_t)lp * lp;
+        for (int q = 0; q < splits; ++q) s += (double)p[q * stride];
+        G[e] = s;
+    }
+}
+
+// X[j][c] = sum_s part[s][j][c]; centring: X[j][c] -= (X[j][l] / m) * qsum[c] (c < l);
+// padding columns zeroed.  qsum[c] = sum of the Q column-sum partials.
+__global__ void __launch_bounds__(256)
+adjoint_reduce_kernel(const float *__restrict__ part, int splits, int64_t rows, int l, int lp,
+                      float *__restrict__ X, int centre, float inv_m,
+                      const float *__restrict__ qpart, int qchunks) {
+    __shared__ float qsum[RPCA_MAX_L];
+    if (centre) {
+        for (int c = threadIdx.x; c < l; c += blockDim.x) {
+            float s = 0.f, comp = 0.f;            // compensated sum of the partials
+            for (int q = 0; q < qchunks; ++q) {
+                const float y = qpart[(int64_t)q * l + c] - comp;
+                const float t = s + y;
+                comp = (t - s) - y;
+                s = t;
+            }
+            qsum[c] = s;
+        }
+        __syncthreads();
+    }
+    const int64_t stride = rows * lp;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; j < rows;
+         j += (int64_t)gridDim.x * blockDim.y) {
+        const float *p = part + j * lp;
+        float cj = 0.f;
+        if (centre) {
+            float s = 0.f;
+            for (int q = 0; q < splits; ++q) s += p[q * stride + l];
+            cj = s * inv_m;
+        }
+        for (int c = threadIdx.x; c < lp; c += blockDim.x) {
+            float v = 0.f;
+            if (c < l) {
+                float s = 0.f, comp = 0.f;
+                for (int q = 0; q < splits; ++q) {
+                    const float y = p[q * stride + c] - comp;
+                    const float t = s + y;
+                    comp = (t - s) - y;
+                    s = t;
+                }
+                v = centre ? s - cj * qsum[c] : s;
+            }
+            X[j * lp + c] = v;
+        }
+    }
+}
+
+__global__ void fill_kernel(float *p, int64_t count, float value) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        p[e] = value;
+}
+
+}  // namespace
+
+int colsum_chunks(int64_t rows) { return (int)cdiv(std::max<int64_t>(rows, 1), kChunkRows); }
+
+int launch_colsum_partial(const float *Y, int64_t rows, int l, int64_t ld, float *part,
+                          int *nchunks, cudaStream_t s) {
+    const int nc = colsum_chunks(rows);
+    if (nchunks) *nchunks = nc;
+    colsum_kernel<<<nc, 256, 0, s>>>(const_cast<float *>(Y), rows, l, ld, part, 0, 0.f);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value, float *part,
+                    cudaStream_t s) {
+    const int nc = colsum_chunks(rows);
+    colsum_kernel<<<nc, 256, 0, s>>>(Q, rows, l, ld, part, 1, ones_value);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, int nchunks,
+                  cudaStream_t s) {
+    const int64_t grid = std::min<int64_t>(cdiv(rows * ld, 256), (int64_t)num_sms() * 4);
+    center_kernel<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(Y, rows, l, ld, part, nchunks);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s) {
+    const int64_t grid = std::min<int64_t>(cdiv((int64_t)l * l, 256), (int64_t)num_sms() * 2);
+    gram_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(part, splits, l, lp, G);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, int lp, float *X,
+                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s) {
+    dim3 block(32, 8);
+    const int64_t grid = std::min<int64_t>(cdiv(rows, 8), (int64_t)num_sms() * 8);
+    adjoint_reduce_kernel<<<(unsigned)std::max<int64_t>(grid, 1), block, 0, s>>>(
+        part, splits, rows, l, lp, X, centre, (float)(1.0 / m), qpart, qchunks);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_fill(float *p, int64_t count, float value, cudaStream_t s) {
+    if (count <= 0) return RPCA_OK;
+    const int64_t grid = std::min<int64_t>(cdiv(count, 256), (int64_t)num_sms() * 8);
+    fill_kernel<<<(unsigned)grid, 256, 0, s>>>(p, count, value);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+}  // namespace rpca

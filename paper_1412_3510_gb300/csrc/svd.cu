@@ -1,0 +1,254 @@
+// SVD of the small factor (Eq. i3) and the lift U = Q W (Eq. i4).
+//
+// B = Q^* A_c is l x n.  The library forms B^* = A_c^* Q (n x l) with the
+// adjoint product, factors it as B^* = Q2 R (CholeskyQR), and then needs only
+// the SVD of the l x l triangular R^T = W Sigma Z^T, since
+// B = R^T Q2^T = W Sigma (Q2 Z)^T.  So U = Q W and V = Q2 Z.
+//
+// The l x l SVD is one-sided Jacobi (Hestenes; Demmel & Veselic 1992): plane
+// rotations applied on the right orthogonalise the columns of M = R^T.  One
+// CTA holds M in shared memory (column j of M is row j of R, contiguous) and
+// runs the l/2 disjoint rotations of a round-robin step in parallel, eight
+// lanes per column pair.  The rotations are logged; a second kernel replays
+// them on the rows of the identity (every row of Z evolves independently) in
+// parallel across CTAs, which keeps Z out of the Jacobi CTA's shared memory.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace rpca {
+
+namespace {
+
+constexpr int kJacThreads = 1024;
+constexpr int kMaxSweeps = 40;
+
+__host__ __device__ __forceinline__ int even_up(int l) { return l + (l & 1); }
+
+// Circle-method round robin over L = even_up(l) players: player 0 fixed,
+// the others rotate; pair g of step r.
+__device__ __forceinline__ void rr_pair(int L, int r, int g, int &p, int &q) {
+    auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (L - 1); };
+    const int a = player(g), b = player(L - 1 - g);
+    p = min(a, b);
+    q = max(a, b);
+}
+
+__global__ void __launch_bounds__(kJacThreads)
+jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int *__restrict__ sweeps_out,
+              float *__restrict__ sig, int *__restrict__ perm, float *__restrict__ Wk, int lp, int k,
+              int kp, DevStatus *__restrict__ st) {
+    extern __shared__ float Ms[];      // l rows of length ldm: row j = column j of M = R^T
+    const int ldm = l + 1;
+    __shared__ int s_rot;
+    __shared__ float s_sig[RPCA_MAX_L];
+    const int tid = threadIdx.x;
+    const int L = even_up(l);
+    const int npairs = L / 2;
+
+    for (int e = tid; e < l * l; e += blockDim.x) Ms[(e / l) * ldm + (e % l)] = R[e];
+    __syncthreads();
+
+    const int g = tid >> 3, lane = tid & 7;
+    const float tol = 8.0f * sqrtf((float)l) * 0x1p-24f;
+    int sweep = 0;
+    for (; sweep < kMaxSweeps; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int step = 0; step < L - 1; ++step) {
+            int p = 0, q = 0;
+            const bool live = g < npairs;
+            if (live) rr_pair(L, step, g, p, q);
+            const bool valid = live && q < l;
+            float a = 0.f, b = 0.f, c = 0.f;
+            if (valid) {
+                const float *mp = Ms + p * ldm, *mq = Ms + q * ldm;
+                for (int e = lane; e < l; e += 8) {
+                    const float x = mp[e], y = mq[e];
+                    a = fmaf(x, x, a);
+                    b = fmaf(y, y, b);
+                    c = fmaf(x, y, c);
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, off);
+                b += __shfl_xor_sync(0xffffffffu, b, off);
+                c += __shfl_xor_sync(0xffffffffu, c, off);
+            }
+            float cs = 1.f, sn = 0.f;
+            if (valid && fabsf(c) > tol * sqrtf(a * b) && c != 0.f) {
+                const float zeta = (b - a) / (2.f * c);
+                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(zeta, 1.f));
+                cs = rsqrtf(fmaf(t, t, 1.f));
+                sn = cs * t;
+                float *mp = Ms + p * ldm, *mq = Ms + q * ldm;
+                for (int e = lane; e < l; e += 8) {
+                    const float x = mp[e], y = mq[e];
+                    mp[e] = cs * x - sn * y;
+                    mq[e] = sn * x + cs * y;
+                }
+                if (lane == 0) atomicAdd(&s_rot, 1);
+            }
+            if (live && lane == 0)
+                rot[((size_t)sweep * (L - 1) + step) * npairs + g] = make_float2(cs, sn);
+            __syncthreads();
+        }
+        if (s_rot == 0) { ++sweep; break; }
+        __syncthreads();
+    }
+    // sweep = number of logged sweeps (the last one made no rotation, or the cap was hit)
+    if (tid == 0) {
+        *sweeps_out = sweep;
+        st->jacobi_sweeps = sweep;
+        if (sweep >= kMaxSweeps && s_rot != 0) atomicAdd(&st->jacobi_unconverged, 1);
+    }
+
+    // singular values = column norms; sort descending (ties by index)
+    // (warp-uniform trip count: every lane reaches the full-mask shuffles)
+    for (int j0 = 0; j0 < l; j0 += kJacThreads / 8) {
+        const int j = j0 + g;
+        float s2 = 0.f;
+        if (j < l)
+            for (int e = lane; e < l; e += 8) s2 = fmaf(Ms[j * ldm + e], Ms[j * ldm + e], s2);
+        for (int off = 1; off < 8; off <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+        if (j < l && lane == 0) s_sig[j] = sqrtf(s2);
+    }
+    __syncthreads();
+    for (int j = tid; j < l; j += blockDim.x) {
+        const float sj = s_sig[j];
+        int rank = 0;
+        for (int i = 0; i < l; ++i) {
+            const float si = s_sig[i];
+            rank += (si > sj) || (si == sj && i < j);
+        }
+        perm[rank] = j;
+        sig[rank] = sj;
+    }
+    __syncthreads();
+    // Wk[i][r] = M[:, perm[r]][i] / sigma_r  (rows >= l and columns >= k zero)
+    for (int e = tid; e < lp * kp; e += blockDim.x) {
+        const int i = e / kp, r = e % kp;
+        float v = 0.f;
+        if (i < l && r < k) {
+            const int j = perm[r];
+            const float s = s_sig[j];
+            v = s > 0.f ? Ms[j * ldm + i] / s : 0.f;
+        }
+        Wk[e] = v;
+    }
+}
+
+// Z = product of the logged rotations applied to the identity; each CTA owns
+// `rows` rows of Z.  Zk[i][r] = Z[i][perm[r]].
+constexpr int kReplayRows = 2;
+
+__global__ void __launch_bounds__(256)
+replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr, int l,
+              const int *__restrict__ perm, float *__restrict__ Zk, int lp, int k, int kp) {
+    __shared__ float Z[kReplayRows][RPCA_MAX_L + 1];
+    const int L = even_up(l), npairs = L / 2;
+    const int i0 = blockIdx.x * kReplayRows;
+    for (int e = threadIdx.x; e < kReplayRows * l; e += blockDim.x) {
+        const int rr = e / l, c = e % l;
+        Z[rr][c] = (i0 + rr == c) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const int sweeps = *sweeps_ptr;
+    const int tasks = kReplayRows * npairs;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int step = 0; step < L - 1; ++step) {
+            const float2 *rs = rot + ((size_t)sw * (L - 1) + step) * npairs;
+            for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+                const int rr = t / npairs, g = t % npairs;
+                auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (L - 1); };
+                const int a = player(g), b = player(L - 1 - g);
+                const int p = min(a, b), q = max(a, b);
+                if (q < l) {
+                    const float2 csn = rs[g];
+                    const float x = Z[rr][p], y = Z[rr][q];
+                    Z[rr][p] = csn.x * x - csn.y * y;
+                    Z[rr][q] = csn.y * x + csn.x * y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < kReplayRows * kp; e += blockDim.x) {
+        const int rr = e / kp, r = e % kp;
+        const int i = i0 + rr;
+        if (i >= lp) continue;
+        float v = 0.f;
+        if (i < l && r < k) v = Z[rr][perm[r]];
+        Zk[(size_t)i * kp + r] = v;
+    }
+}
+
+// Per column r < k: flip V[:, r] when its largest-|entry| (first on ties) is
+// negative; apply the same sign to Wk[:, r]; S[r] = sig[r].
+__global__ void __launch_bounds__(256)
+sign_fix_kernel(float *__restrict__ V, int64_t n, int64_t ldv, float *__restrict__ Wk, int lp, int kp,
+                const float *__restrict__ sig, float *__restrict__ S) {
+    const int r = blockIdx.x;
+    __shared__ float sv[256];
+    __shared__ int64_t si[256];
+    float best = -1.f;
+    int64_t bi = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float a = fabsf(V[i * ldv + r]);
+        if (a > best) { best = a; bi = i; }      // strictly greater keeps the first index
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            const float ob = sv[threadIdx.x + off];
+            const int64_t oi = si[threadIdx.x + off];
+            if (ob > sv[threadIdx.x] || (ob == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = ob;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const bool flip = n > 0 && V[si[0] * ldv + r] < 0.f;
+    __syncthreads();
+    if (flip) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i * ldv + r] = -V[i * ldv + r];
+        for (int i = threadIdx.x; i < lp; i += blockDim.x) Wk[(size_t)i * kp + r] = -Wk[(size_t)i * kp + r];
+    }
+    if (threadIdx.x == 0) S[r] = sig[r];
+}
+
+}  // namespace
+
+size_t small_svd_rot_floats(int l) {
+    const int L = even_up(l);
+    return (size_t)kMaxSweeps * (L - 1) * (L / 2) * 2;
+}
+
+int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, float *Zk, float *sig,
+                     float *rot, float *zbuf, int *perm, DevStatus *st, cudaStream_t s) {
+    int *sweeps = reinterpret_cast<int *>(zbuf);
+    const size_t smem = (size_t)l * (l + 1) * sizeof(float);
+    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) * sizeof(float)));
+    jacobi_kernel<<<1, kJacThreads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig,
+                                               perm, Wk, lp, k, kp, st);
+    RPCA_CHECK_LAUNCH();
+    const int grid = (int)cdiv(lp, kReplayRows);
+    replay_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk, lp,
+                                       k, kp);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_sign_fix(float *V, int64_t n, int64_t ldv, int k, float *Wk, int lp, int kp,
+                    const float *sig, float *S, cudaStream_t s) {
+    sign_fix_kernel<<<k, 256, 0, s>>>(V, n, ldv, Wk, lp, kp, sig, S);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+}  // namespace rpca

@@ -1,0 +1,151 @@
+"""Python binding of librpca.so: the C-ABI entry points under the same names.
+
+Argument marshalling only.  Every step of the method runs in the library's CUDA
+kernels; PyTorch supplies device memory (outputs, workspace) and the current
+stream.  Nothing here computes, and there is no CPU fallback: a missing
+library or a CPU tensor raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+class RpcaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        lib = L.load()
+        msg = lib.rpca_status_string(code).decode()
+        super().__init__(f"{what}: {msg} (status {code})" if what else f"{msg} (status {code})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code < 0:
+        raise RpcaError(code, what)
+    return code
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+
+
+def _rowmajor_ld(t: torch.Tensor, name: str) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D with unit column stride (row-major)")
+    return max(t.stride(0), t.shape[1])
+
+
+def make_opts(k, l=None, its=2, raw=False, seed=0, precision="fp32", renorm="cholqr",
+              omega=None, col_weights=None) -> L.RpcaOpts:
+    o = L.RpcaOpts()
+    o.k = int(k)
+    o.l = int(k + 2 if l is None else l)
+    o.its = int(its)
+    o.raw = int(bool(raw))
+    o.seed = int(seed) & ((1 << 64) - 1)
+    o.precision = L.PREC[precision]
+    o.renorm = L.RENORM[renorm]
+    o.omega = None if omega is None else omega.data_ptr()
+    o.col_weights = None if col_weights is None else col_weights.data_ptr()
+    return o
+
+
+def rpca_dense_workspace_size(m: int, n: int, opts: L.RpcaOpts) -> int:
+    return int(L.load().rpca_dense_workspace_size(m, n, C.byref(opts)))
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """A 256-byte-aligned device buffer of nbytes (torch allocations are 512-aligned)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw: bool = False,
+               seed: int = 0, precision: str = "fp32", renorm: str = "cholqr",
+               omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
+               ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+    """Randomized PCA A_c ~ U diag(S) V^T (Sections 2 and 5 of the paper).
+
+    A: m x n float32 CUDA tensor, row-major (any leading dimension >= n).
+    Returns (U m x k, S k, V n x k).  With check=True the device status word
+    is read after the call (one stream synchronisation).
+    """
+    _need_cuda(A, "A")
+    lda = _rowmajor_ld(A, "A")
+    m, n = A.shape
+    if omega is not None:
+        _need_cuda(omega, "omega")
+        omega = omega.contiguous()
+    if col_weights is not None:
+        _need_cuda(col_weights, "col_weights")
+        col_weights = col_weights.contiguous()
+    opts = make_opts(k, l, its, raw, seed, precision, renorm, omega, col_weights)
+    lib = L.load()
+    need = rpca_dense_workspace_size(m, n, opts)
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_dense_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if out is None:
+        U = torch.empty(m, k, dtype=torch.float32, device=A.device)
+        S = torch.empty(k, dtype=torch.float32, device=A.device)
+        V = torch.empty(n, k, dtype=torch.float32, device=A.device)
+    else:
+        U, S, V = out
+    ldu = _rowmajor_ld(U, "U")
+    ldv = _rowmajor_ld(V, "V")
+    st = _stream(stream)
+    code = lib.rpca_dense(_ptr(A), m, n, lda, C.byref(opts), _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                          _ptr(ws), ws.numel(), st)
+    _check(code, "rpca_dense")
+    if check:
+        status = rpca_read_status(ws, stream)
+        _check(status, "rpca_dense (device)")
+    return U, S, V
+
+
+def rpca_read_status(ws: torch.Tensor, stream=None) -> int:
+    out = C.c_int32(0)
+    _check(L.load().rpca_read_status(_ptr(ws), _stream(stream), C.byref(out)), "rpca_read_status")
+    return int(out.value)
+
+
+def read_status_block(ws: torch.Tensor) -> dict:
+    """The device status block's counters (shifts, Jacobi sweeps...) after a synchronisation."""
+    torch.cuda.current_stream(ws.device).synchronize()
+    v = ws[:256].view(torch.int32).cpu().tolist()
+    return {"status": v[0], "flags": v[1], "shifts": v[2], "jacobi_sweeps": v[3],
+            "jacobi_unconverged": v[4], "timeouts": v[5]}
+
+
+def rpca_gaussian_omega(n: int, l: int, seed: int, stream_id: int = 0, device="cuda", stream=None):
+    out = torch.empty(n, l, dtype=torch.float32, device=device)
+    _check(L.load().rpca_gaussian_omega(n, l, seed & ((1 << 64) - 1), stream_id, _ptr(out), l,
+                                        _stream(stream)), "rpca_gaussian_omega")
+    return out
+
+
+def rpca_philox4x64_10(key0: int, key1: int, first: int, nblocks: int, device="cuda", stream=None):
+    out = torch.empty(nblocks, 4, dtype=torch.int64, device=device)
+    m64 = (1 << 64) - 1
+    _check(L.load().rpca_philox4x64_10(key0 & m64, key1 & m64, first & m64, nblocks, _ptr(out),
+                                       _stream(stream)), "rpca_philox4x64_10")
+    return out
+
+
+def rpca_launch_count() -> int:
+    return int(L.load().rpca_launch_count())
