@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 randomized PCA (Szlam, Kluger & Tygert 2014, Sections 2 and 5).
+
+One step = one whole rank-k PCA of the workload (test matrix, sketch, power
+iterations with renormalisations, projection, small SVD, lift) through the
+library's C ABI, with A already resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16x3]
+                  [--workload NAME] [--impl ours|reference]
+
+Multi-GPU: the path is one PCA per GPU (independent replicas, no exchange);
+under torchrun every rank runs its own PCAs and value = PCAs of all ranks /
+the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rank-k PCAs/s and GB/s per pass over A at resid <=1.1*sigma_{k+1}, vs plain FP32 GPU"
+DEFAULT_WORKLOAD = "dense_100000x2000_k100"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT = 152
+FP32_FMA_PER_SM_CLK = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    d = dict(FALLBACK_PEAKS)
+    d["source"] = "fallback"
+    d["sm_max_mhz"] = 2070.0
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1 + 0.1]
+        if not inside and rows and self.t0:
+            inside = [min(rows, key=lambda r: abs(r[0] - self.t0))]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[2]) for _, p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in inside for i in range(4) if p[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(inside[0][1][3]),
+                "reasons": reasons, "samples": len(inside),
+                "power_w_max": max((num(p[4]) or 0.0) for _, p in inside)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name, device, rank):
+    import numpy as np
+    import synth
+    w = dict(synth.WORKLOADS[name])
+    r = min(w["m"], w["n"])
+    sigma = w["spectrum"](r)
+    A = synth.haar_dense_torch(w["m"], w["n"], sigma, w["seed"], device=device)
+    return w, A, np.asarray(sigma)
+
+
+def sigma_k1_reference(A, k, raw):
+    """sigma_{k+1} of A_c from the FP64 Gram of the centred matrix (measurement only)."""
+    import torch
+    n = A.shape[1]
+    G = torch.zeros(n, n, dtype=torch.float64, device=A.device)
+    mean = A.double().mean(0) if not raw else None
+    for i in range(0, A.shape[0], 8192):
+        blk = A[i:i + 8192].double()
+        if mean is not None:
+            blk = blk - mean
+        G.addmm_(blk.T, blk)
+    ev = torch.linalg.eigvalsh(G).flip(0).clamp_min(0).sqrt()
+    return float(ev[k].item())
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel_key, sha):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if e and e.get("src_sha") == sha:
+        return e.get("traffic_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(A_host, w, rows):
+    import oracle
+    sub = A_host[:rows]
+    t = time.perf_counter()
+    oracle.rpca(sub, w["k"], w["l"], w["its"], raw=w["raw"], seed=1)
+    return time.perf_counter() - t
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """The oracle on the host cores, each step a bounded row sample of the workload."""
+    import numpy as np
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = dict(synth.WORKLOADS[args.workload])
+    r = min(w["m"], w["n"])
+    # size each step's row sample so that warmup + steps take about ref_budget seconds
+    probe_rows = max(w["l"] + 1, min(w["m"], 4000))
+    A = synth.haar_dense_np(min(w["m"], max(probe_rows, int(args.ref_rows))), w["n"], w["spectrum"](r), w["seed"])
+    t_probe = oracle_sample(A, w, probe_rows)
+    per_row = t_probe / probe_rows
+    rows = int(args.ref_budget / max(args.steps + args.warmup, 1) / max(per_row, 1e-9))
+    rows = max(w["l"] + 1, min(rows, A.shape[0]))
+    for _ in range(args.warmup):
+        oracle_sample(A, w, rows)
+    ts = [oracle_sample(A, w, rows) for _ in range(args.steps)]
+    per_full = (sum(ts) / len(ts)) * (w["m"] / rows)
+    value = 1.0 / per_full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "PCA/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"],
+                   "its": w["its"], "raw": w["raw"]},
+        "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"FP64 numpy oracle on the first {rows} of {w['m']} rows, time scaled by m"},
+        "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--resid-iters", type=int, default=20)
+    ap.add_argument("--ref-rows", type=int, default=50000)
+    ap.add_argument("--ref-budget", type=float, default=150.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_1412_3510_gb300 import build as B
+    B.build()
+    import paper_1412_3510_gb300 as rp
+
+    w, A, sigma = make_workload(args.workload, dev, rank)
+    m, n, k, l, its, raw = w["m"], w["n"], w["k"], w["l"], w["its"], w["raw"]
+    opts = rp.make_opts(k, l, its, raw, seed=1 + rank, precision=args.precision)
+    ws = rp.workspace(rp.rpca_dense_workspace_size(m, n, opts), dev)
+    U = torch.empty(m, k, device=dev)
+    S = torch.empty(k, device=dev)
+    V = torch.empty(n, k, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rp.rpca_dense(A, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
+                      out=(U, S, V), check=False)
+
+    for _ in range(args.warmup):
+        step()
+    status = rp.rpca_read_status(ws)
+    block = rp.read_status_block(ws)
+
+    # accuracy check outside the timed region: resid <= 1.1 sigma_{k+1}
+    est = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
+    sk1 = sigma_k1_reference(A, k, raw)
+
+    # timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    rp.rpca_timing_reset()
+    rp.rpca_timing_enable(True, reserve=2 * (2 * its + 3) * args.steps + 64)
+    launches0 = rp.rpca_launch_count()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler.mark("t0")
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    barrier()
+    sampler.mark("t1")
+    launches = rp.rpca_launch_count() - launches0
+    rp.rpca_timing_enable(False)
+    sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = world * args.steps / (ms_total / 1e3)
+    n_apply, t_apply = rp.rpca_timing_read(0)
+    n_adj, t_adj = rp.rpca_timing_read(1)
+    n_svd, t_svd = rp.rpca_timing_read(3)
+    rp.rpca_timing_reset()
+
+    # roofline of the dominant kernel (the passes over A)
+    pk = peaks()
+    a_bytes = 4.0 * m * n
+    pass_bytes = a_bytes + 4.0 * (m + n) * l        # A + the block read + the block written
+    pass_flops = 2.0 * m * n * l
+    passes = n_apply + n_adj
+    avg_pass_ms = (t_apply + t_adj) / max(passes, 1)
+    gbs_per_pass = pass_bytes / (avg_pass_ms * 1e-3) / 1e9
+    kernel_files = ["paper_1412_3510_gb300/csrc/gemm_simt.cu"]
+    if args.precision == "fp32":
+        peak = SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = pass_flops / (avg_pass_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
+                "kernel": "sgemm_kernel (A X and A^T Q passes)"}
+        key = "sgemm_pass_fp32"
+    else:
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": gbs_per_pass, "peak": peak, "unit": "GB/s", "frac": gbs_per_pass / peak,
+                "peak_source": pk["source"], "kernel": "tcgen05 pass kernels"}
+        key = "tc_pass_bf16x3"
+    sha = source_sha(kernel_files)
+    roof["traffic"] = traffic_from_profiles(key, sha)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_host = A.cpu().pin_memory()
+        U_h = torch.empty(m, k).pin_memory()
+        S_h = torch.empty(k).pin_memory()
+        V_h = torch.empty(n, k).pin_memory()
+        A_dev = torch.empty_like(A)
+        for _ in range(2):
+            A_dev.copy_(A_host, non_blocking=True)
+            rp.rpca_dense(A_dev, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
+                          out=(U, S, V), check=False)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            A_dev.copy_(A_host, non_blocking=True)
+            rp.rpca_dense(A_dev, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
+                          out=(U, S, V), check=False)
+            U_h.copy_(U, non_blocking=True)
+            S_h.copy_(S, non_blocking=True)
+            V_h.copy_(V, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * args.e2e_steps / (e2e_ms / 1e3), "unit": "PCA/s",
+               "h2d_bytes_per_step": int(A.numel() * 4), "d2h_bytes_per_step": int((m * k + k + n * k) * 4)}
+        del A_host, A_dev
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_host = A[: min(m, args.ref_rows)].cpu().numpy()
+        rows = A_host.shape[0]
+        t = oracle_sample(A_host, w, rows)
+        cpu = {"value": 1.0 / (t * m / rows), "unit": "PCA/s", "cores": cores(), "kind": "oracle",
+               "sample": f"one FP64 numpy oracle PCA on the first {rows} of {m} rows "
+                         f"({t:.1f} s), time scaled by m"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "PCA/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "its": its, "raw": raw,
+                   "precision": args.precision, "renorm": "cholqr",
+                   "A_bytes": int(a_bytes), "l2": "A (%.0f MB) is larger than L2 (129 MB); no flush" % (a_bytes / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "gbs_per_pass": gbs_per_pass,
+        "passes_per_step": passes / args.steps,
+        "stage_ms_per_step": {"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,
+                              "small_svd": t_svd / args.steps},
+        "accuracy": {"resid_est": est, "sigma_k1": sk1, "resid_over_sigma_k1": est / sk1,
+                     "resid_ok": bool(est <= 1.1 * sk1), "status": status, "shifts": block["shifts"],
+                     "jacobi_sweeps": block["jacobi_sweeps"]},
+        "clocks": sampler.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

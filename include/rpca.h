@@ -135,6 +135,20 @@ int rpca_resid_norm(const float *A, int64_t m, int64_t n, int64_t lda, int32_t r
                     void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * One product of the method alone (the sketch's A Omega, either half of a
+ * power iteration, or B^* = A^* Q; Sections 2 and 5), without centring:
+ *   adjoint == 0:  C (m x w) = A B,   B n x w;
+ *   adjoint != 0:  C (n x w) = A^T B, B m x w.
+ * B and C are row-major with leading dimension w; w is a multiple of 8 and
+ * at most 256.  precision selects the FP32 FFMA or the tcgen05 split-BF16
+ * kernels (the latter need A 16-byte aligned and lda % 4 == 0, else the FP32
+ * kernels run).  ws: rpca_dense_pass_workspace_size bytes, 256-byte aligned.
+ * ---------------------------------------------------------------------- */
+size_t rpca_dense_pass_workspace_size(int64_t m, int64_t n, int32_t w, int32_t adjoint, int32_t precision);
+int rpca_dense_pass(const float *A, int64_t m, int64_t n, int64_t lda, int32_t adjoint, const float *B,
+                    int32_t w, float *C, int32_t precision, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * The sketch's test matrix alone (Section 2; the step every call starts with).
  * Writes Omega (n x l, row-major, leading dimension ldo >= l, device): entry
  * (i, j) is element e = i*l + j of the stream in which Philox4x64-10 block b
@@ -157,6 +171,22 @@ const char *rpca_status_string(int status);
 
 /* Number of kernels this library has launched in this process. */
 int64_t rpca_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Stage timing for benchmarks (off by default).  While enabled, the launches
+ * of each timed stage are bracketed by CUDA events on their stream:
+ *   kind 0 = products A X (the sketch and the A half of each power iteration),
+ *   kind 1 = adjoint products A^T Q (the A^* half and B^* = A_c^* Q),
+ *   kind 3 = small SVD (Jacobi + rotation replay).
+ * rpca_timing_read waits for the recorded events and returns the number of
+ * timed launches of `kind` since the last reset and their summed duration.
+ * rpca_timing_enable(on): 0 = off, 1 = on, > 1 = on and create that many
+ * events up front so that none is created inside the timed window.
+ * Host-side state; not for use during CUDA graph capture.
+ * ---------------------------------------------------------------------- */
+int rpca_timing_enable(int32_t on);
+int rpca_timing_reset(void);
+int rpca_timing_read(int32_t kind, int64_t *count, double *total_ms);
 
 #ifdef __cplusplus
 }

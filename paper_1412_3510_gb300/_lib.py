@@ -42,11 +42,16 @@ SIGNATURES = [
     ("rpca_resid_workspace_size", _SZ, [_I64, _I64, _I32]),
     ("rpca_resid_norm", C.c_int, [_P, _I64, _I64, _I64, _I32, _P, _I64, _P, _P, _I64, _I32, _I32, _U64,
                                   _P, _P, _SZ, _P]),
+    ("rpca_dense_pass_workspace_size", _SZ, [_I64, _I64, _I32, _I32, _I32]),
+    ("rpca_dense_pass", C.c_int, [_P, _I64, _I64, _I64, _I32, _P, _I32, _P, _I32, _P, _SZ, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
     ("rpca_status_string", C.c_char_p, [C.c_int]),
     ("rpca_launch_count", C.c_int64, []),
+    ("rpca_timing_enable", C.c_int, [_I32]),
+    ("rpca_timing_reset", C.c_int, []),
+    ("rpca_timing_read", C.c_int, [_I32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 ]
 
 _lib = None

@@ -1,21 +1,43 @@
 // Dense entry point: A is an m x n FP32 row-major matrix (leading dimension lda).
 #include "pipeline.cuh"
+#include "resid.cuh"
+#include "tc_gemm.cuh"
 
 namespace rpca {
 
 namespace {
 
+// The two passes over A.  FP32: register-blocked FFMA kernels.  BF16X3: the
+// tcgen05 split-BF16 kernels (the block operand is split once per pass into
+// the operator's scratch); A must then be 16-byte aligned with lda % 4 == 0.
 struct DenseOp final : Operator {
     const float *A = nullptr;
     int64_t lda = 0;
     int precision = RPCA_PREC_FP32;
 
+    bool tc(int lp) const { return precision == RPCA_PREC_BF16X3 && tc_supported(A, lda, lp); }
+    size_t scratch_bytes(int lp) const override {
+        if (precision != RPCA_PREC_BF16X3) return 0;
+        return std::max(tc_split_bytes(n, lp), tc_split_bytes(m, lp));
+    }
     int apply(const float *X, int lp, float *Y, cudaStream_t s) const override {
+        if (tc(lp)) {
+            auto *xs = reinterpret_cast<__nv_bfloat16 *>(scratch);
+            RPCA_TRY(launch_tc_split(X, n, lp, xs, s));
+            return launch_tc_apply(A, m, n, lda, xs, lp, Y, st, s);
+        }
         return launch_sgemm(false, m, lp, n, A, lda, X, lp, Y, lp, 1, 0, s);
     }
-    int adjoint_splits(int lp) const override { return choose_splits(n, lp, m); }
+    int adjoint_splits(int lp) const override {
+        return tc(lp) ? tc_adjoint_splits(n, m, lp) : choose_splits(n, lp, m);
+    }
     int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const override {
         const int sp = adjoint_splits(lp);
+        if (tc(lp)) {
+            auto *qs = reinterpret_cast<__nv_bfloat16 *>(scratch);
+            RPCA_TRY(launch_tc_split(Q, m, lp, qs, s));
+            return launch_tc_adjoint(A, m, n, lda, qs, lp, part, sp, st, s);
+        }
         return launch_sgemm(true, n, lp, m, A, lda, Q, lp, part, lp, sp, n * (int64_t)lp, s);
     }
 };
@@ -27,7 +49,12 @@ struct DenseOp final : Operator {
 extern "C" size_t rpca_dense_workspace_size(int64_t m, int64_t n, const rpca_opts *o) {
     if (!o || m < 1 || n < 1 || o->l < 1 || o->k < 1 || o->l > RPCA_MAX_L) return 0;
     const int lp = rpca::padded_l(o->l);
-    return rpca::make_layout(m, n, o->l, o->k, rpca::choose_splits(n, lp, m)).total;
+    // sized for the larger of the two forms' partial buffers so that the
+    // same workspace serves either precision
+    const int splits = std::max(rpca::choose_splits(n, lp, m), rpca::tc_adjoint_splits(n, m, lp));
+    rpca::DenseOp op;
+    op.m = m; op.n = n; op.precision = o->precision;
+    return rpca::make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp)).total;
 }
 
 extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, const rpca_opts *o,
@@ -36,10 +63,83 @@ extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, con
     if (!A || !o || lda < n) return RPCA_ERR_INVALID_ARG;
     const size_t need = rpca_dense_workspace_size(m, n, o);
     RPCA_TRY(rpca::check_common(m, n, o, U, ldu, S, V, ldv, ws, ws_bytes, need));
-    if (o->precision != RPCA_PREC_FP32 || o->renorm != RPCA_RENORM_CHOLQR) return RPCA_ERR_UNSUPPORTED;
+    if (o->renorm != RPCA_RENORM_CHOLQR) return RPCA_ERR_UNSUPPORTED;
     rpca::DenseOp op;
     op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
     const int lp = rpca::padded_l(o->l);
-    const rpca::Layout L = rpca::make_layout(m, n, o->l, o->k, op.adjoint_splits(lp));
+    const int splits = std::max(rpca::choose_splits(n, lp, m), rpca::tc_adjoint_splits(n, m, lp));
+    const rpca::Layout L = rpca::make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp));
     return rpca::run_pipeline(op, o, U, ldu, S, V, ldv, ws, L, (cudaStream_t)stream);
+}
+
+extern "C" size_t rpca_resid_workspace_size(int64_t m, int64_t n, int32_t k) {
+    if (m < 1 || n < 1 || k < 0 || k > RPCA_MAX_L) return 0;
+    return rpca::make_resid_layout(m, n, k, rpca::choose_splits(n, 8, m)).total;
+}
+
+extern "C" int rpca_resid_norm(const float *A, int64_t m, int64_t n, int64_t lda, int32_t raw,
+                               const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv,
+                               int32_t k, int32_t iters, uint64_t seed, double *est, void *ws,
+                               size_t ws_bytes, rpca_stream_t stream) {
+    if (!A || !est || m < 1 || n < 1 || lda < n || k < 0 || k > RPCA_MAX_L || iters < 1) return RPCA_ERR_INVALID_ARG;
+    if (k > 0 && (!U || !S || !V || ldu < k || ldv < k)) return RPCA_ERR_INVALID_ARG;
+    const size_t need = rpca_resid_workspace_size(m, n, k);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
+    rpca::DenseOp op;
+    op.m = m; op.n = n; op.A = A; op.lda = lda;
+    const rpca::ResidLayout R = rpca::make_resid_layout(m, n, k, op.adjoint_splits(8));
+    return rpca::run_resid(op, raw, U, ldu, S, V, ldv, k, iters, seed, est, ws, R, (cudaStream_t)stream);
+}
+
+namespace {
+
+struct PassPlan {
+    size_t status = 0, part = 0, scratch = 0, total = 0;
+    int splits = 1;
+};
+
+PassPlan pass_plan(const rpca::DenseOp &op, int w, int adjoint) {
+    PassPlan P;
+    auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    P.status = off; off = a256(off + sizeof(rpca::DevStatus));
+    P.splits = adjoint ? std::max(op.adjoint_splits(w), 1) : 1;
+    // room for either form's number of partial slices
+    const int most = std::max(rpca::choose_splits(op.n, w, op.m), rpca::tc_adjoint_splits(op.n, op.m, w));
+    P.part = off; off = a256(off + (adjoint ? (size_t)most * op.n * w * 4 : 0));
+    P.scratch = off; off = a256(off + op.scratch_bytes(w));
+    P.total = off;
+    return P;
+}
+
+}  // namespace
+
+extern "C" size_t rpca_dense_pass_workspace_size(int64_t m, int64_t n, int32_t w, int32_t adjoint,
+                                                 int32_t precision) {
+    if (m < 1 || n < 1 || w < 8 || w > 256 || w % 8) return 0;
+    rpca::DenseOp op;
+    op.m = m; op.n = n; op.precision = precision;
+    op.A = reinterpret_cast<const float *>(256); op.lda = 4;       // size as if the tensor-core form runs
+    return pass_plan(op, w, adjoint).total;
+}
+
+extern "C" int rpca_dense_pass(const float *A, int64_t m, int64_t n, int64_t lda, int32_t adjoint, const float *B,
+                               int32_t w, float *C, int32_t precision, void *ws, size_t ws_bytes,
+                               rpca_stream_t stream) {
+    if (!A || !B || !C || m < 1 || n < 1 || lda < n || w < 8 || w > 256 || w % 8) return RPCA_ERR_INVALID_ARG;
+    if (precision != RPCA_PREC_FP32 && precision != RPCA_PREC_BF16X3) return RPCA_ERR_INVALID_ARG;
+    const size_t need = rpca_dense_pass_workspace_size(m, n, w, adjoint, precision);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    rpca::DenseOp op;
+    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = precision;
+    const PassPlan P = pass_plan(op, w, adjoint);
+    char *base = reinterpret_cast<char *>(ws);
+    op.st = reinterpret_cast<rpca::DevStatus *>(base + P.status);
+    op.scratch = base + P.scratch;
+    if (cudaMemsetAsync(op.st, 0, sizeof(rpca::DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (!adjoint) return op.apply(B, w, C, s);
+    float *part = reinterpret_cast<float *>(base + P.part);
+    RPCA_TRY(op.adjoint(B, w, part, s));
+    return rpca::launch_adjoint_reduce(part, P.splits, n, w, w, C, 0, (double)m, nullptr, 0, s);
 }

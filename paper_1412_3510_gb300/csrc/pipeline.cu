@@ -15,6 +15,7 @@
 // adjoint product holds ones (it carries m c through A^T), every other padding
 // column holds zeros.
 #include "pipeline.cuh"
+#include "timing.cuh"
 
 namespace rpca {
 
@@ -37,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits) {
+Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_t op_scratch) {
     Layout L;
     L.m = m; L.n = n; L.l = l; L.k = k;
     L.lp = padded_l(l);
@@ -69,6 +70,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits) {
     L.perm = take(lp * 4);
     L.rot = take(small_svd_rot_floats(l) * 4);
     L.zbuf = take(256);
+    L.scratch = take(op_scratch);
     L.total = off;
     return L;
 }
@@ -147,7 +149,10 @@ int renorm_n(const Ctx &c, bool final_) {
 int adjoint_pass(const Operator &op, const Ctx &c, bool raw) {
     const Layout &L = c.L;
     float *part = c.at<float>(L.part);
-    RPCA_TRY(op.adjoint(c.at<float>(L.y1), L.lp, part, c.s));
+    {
+        TimedScope ts(kTimeAdjoint, c.s);
+        RPCA_TRY(op.adjoint(c.at<float>(L.y1), L.lp, part, c.s));
+    }
     const int splits = op.adjoint_splits(L.lp);
     RPCA_TRY(launch_adjoint_reduce(part, std::max(splits, 1), L.n, L.l, L.lp, c.at<float>(L.x0), raw ? 0 : 1,
                                    (double)L.m, c.at<float>(L.qpart), L.cchunks, c.s));
@@ -156,9 +161,11 @@ int adjoint_pass(const Operator &op, const Ctx &c, bool raw) {
 
 }  // namespace
 
-int run_pipeline(const Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
+int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s) {
     Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status)};
+    op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
+    op.st = c.st;
     const bool raw = o->raw != 0;
     const int l = L.l, lp = L.lp;
     float *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
@@ -175,13 +182,17 @@ int run_pipeline(const Operator &op, const rpca_opts *o, float *U, int64_t ldu, 
         RPCA_TRY(launch_omega(L.n, l, o->seed, 0, o->col_weights, x1, lp, s));
     }
 
+    auto apply = [&]() {
+        TimedScope ts(kTimeApply, s);
+        return op.apply(x1, lp, y0, s);
+    };
     // sketch and power iterations
-    RPCA_TRY(op.apply(x1, lp, y0, s));
+    RPCA_TRY(apply());
     RPCA_TRY(renorm_m(c, raw, o->its == 0));
     for (int it = 1; it <= o->its; ++it) {
         RPCA_TRY(adjoint_pass(op, c, raw));
         RPCA_TRY(renorm_n(c, false));
-        RPCA_TRY(op.apply(x1, lp, y0, s));
+        RPCA_TRY(apply());
         RPCA_TRY(renorm_m(c, raw, it == o->its));
     }
 
@@ -189,8 +200,11 @@ int run_pipeline(const Operator &op, const rpca_opts *o, float *U, int64_t ldu, 
     RPCA_TRY(adjoint_pass(op, c, raw));
     RPCA_TRY(renorm_n(c, true));
     float *wk = c.at<float>(L.wk), *zk = c.at<float>(L.zk), *sig = c.at<float>(L.sig);
-    RPCA_TRY(launch_small_svd(c.at<float>(L.racc0), l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
-                              c.at<float>(L.zbuf), c.at<int>(L.perm), c.st, s));
+    {
+        TimedScope ts(kTimeSmallSvd, s);
+        RPCA_TRY(launch_small_svd(c.at<float>(L.racc0), l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
+                                  c.at<float>(L.zbuf), c.at<int>(L.perm), c.st, s));
+    }
 
     // V = Q2 Z_k, signs, U = Q W_k (Eq. i4)
     RPCA_TRY(launch_sgemm(false, L.n, L.k, lp, x1, lp, zk, L.kp, V, ldv, 1, 0, s));

@@ -8,7 +8,10 @@ namespace rpca {
 // The two products the method needs, for one storage format of A.
 struct Operator {
     int64_t m = 0, n = 0;
+    void *scratch = nullptr;          // operator-owned part of the workspace
+    DevStatus *st = nullptr;          // device status block
     virtual ~Operator() = default;
+    virtual size_t scratch_bytes(int lp) const { (void)lp; return 0; }
     // Y (m x lp) = A X (X n x lp); padding columns of X are zero.
     virtual int apply(const float *X, int lp, float *Y, cudaStream_t s) const = 0;
     // part / X: X (n x lp) = A^T Q as `splits` partial slices in `part`
@@ -23,10 +26,10 @@ struct Layout {
     int s_adj = 0, s_gram_m = 0, s_gram_n = 0, cchunks = 0;
     size_t status = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, part = 0, cpart = 0, qpart = 0, G = 0,
            rinv = 0, racc0 = 0, racc1 = 0, wk = 0, zk = 0, sig = 0, perm = 0, rot = 0, zbuf = 0,
-           total = 0;
+           scratch = 0, total = 0;
 };
 
-Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits);
+Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_t op_scratch);
 
 // Validate the arguments common to every entry point.
 int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64_t ldu,
@@ -34,7 +37,7 @@ int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64
                  size_t need);
 
 // Run the whole method (Sections 2 and 5; Eqs. i1-i4) on operator `op`.
-int run_pipeline(const Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
+int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s);
 
 }  // namespace rpca

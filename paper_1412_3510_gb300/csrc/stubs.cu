@@ -5,7 +5,3 @@ extern "C" size_t rpca_csr_workspace_size(int64_t, int64_t, int64_t, const rpca_
 extern "C" int rpca_csr(int64_t, int64_t, int64_t, const int32_t *, const int32_t *, const float *,
                         const rpca_opts *, float *, int64_t, float *, float *, int64_t, void *, size_t,
                         rpca_stream_t) { return RPCA_ERR_UNSUPPORTED; }
-extern "C" size_t rpca_resid_workspace_size(int64_t, int64_t, int32_t) { return 0; }
-extern "C" int rpca_resid_norm(const float *, int64_t, int64_t, int64_t, int32_t, const float *, int64_t,
-                               const float *, const float *, int64_t, int32_t, int32_t, uint64_t, double *,
-                               void *, size_t, rpca_stream_t) { return RPCA_ERR_UNSUPPORTED; }

@@ -1,0 +1,502 @@
+// Passes over A on the tcgen05 tensor cores in split BF16 ("precision form").
+//
+// The products A X (Section 2's sketch and the A half of every power
+// iteration) and A^T Q (the A^* half and B^* = A_c^* Q of Eq. i2) stream the
+// FP32 matrix A once per pass.  Each element is split as a = a_hi + a_lo with
+// a_hi = bf16(a), a_lo = bf16(a - a_hi) (16 significant bits in all); the
+// block operand (X or Q) is split the same way, and three BF16 products
+// a_hi b_hi + a_hi b_lo + a_lo b_hi accumulate in FP32 in tensor memory.
+//
+// One CTA owns a 128-row tile of the output (rows of A for A X, columns of A
+// for A^T Q) and all N <= 256 output columns:
+//   warp 0       TMA loads of FP32 A tiles (128B-swizzled boxes), 3-stage ring
+//   warp 3       bulk copies of the pre-split BF16 block tiles
+//   warps 4..7   split each FP32 stage into BF16 hi/lo in the MMA's canonical
+//                K-major layout (transposing for A^T), then the epilogue
+//   warp 1       TMEM allocation; one lane issues the MMAs
+// Every wait on an mbarrier is bounded; a wait that runs out records
+// RPCA_ERR_TIMEOUT in the status block and the CTA drains and exits.
+#include "internal.cuh"
+#include "tc_gemm.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+namespace rpca {
+
+namespace {
+
+constexpr int kBM = 128;              // MMA M and CTA output rows
+constexpr int kStagesA = 3;           // FP32 A ring depth
+constexpr int kBufs = 2;              // converted BF16 buffers
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at GB300 clocks
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed, false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// UMMA shared-memory descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K,
+// sbo = byte step between 8-row groups; version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: D F32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+// Split 8 floats into hi/lo BF16 octets.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        h[e] = __float2bfloat16_rn(x[e]);
+        l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+    }
+    hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+    lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+}
+
+// Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).
+template <int BK>
+struct Plan {
+    static constexpr uint32_t a32_bytes = kBM * BK * 4;          // FP32 stage
+    static constexpr uint32_t abf_bytes = kBM * BK * 2;          // one of hi / lo
+    uint32_t b_bytes;                                            // one of hi / lo (N x BK bf16)
+    uint32_t off_a32, off_buf, buf_bytes, off_bar, total;
+    __host__ __device__ explicit Plan(int N) {
+        b_bytes = (uint32_t)N * BK * 2;
+        off_a32 = 0;
+        off_buf = kStagesA * a32_bytes;
+        buf_bytes = 2 * abf_bytes + 2 * b_bytes;
+        off_bar = off_buf + kBufs * buf_bytes;
+        total = off_bar + 256;
+    }
+};
+
+struct TcArgs {
+    const __nv_bfloat16 *bsplit;  // pre-split block operand: per stage [hi | lo], each N x BK
+    float *out;                   // output (+ blockIdx.y * split_stride)
+    int64_t out_rows;             // rows of the output that exist (m for A X, n for A^T Q)
+    int64_t ldo;                  // leading dimension of out
+    int ncols_store;              // columns to store (lp)
+    int N;                        // MMA N (multiple of 16, <= 256)
+    int64_t k_begin_stride;       // K elements per split (adjoint), 0 for A X
+    int64_t K;                    // total K (n for A X, m for A^T Q)
+    int64_t split_stride;         // elements between output partials
+    DevStatus *st;
+};
+
+// ADJ = false: out[128 rows of A] = A X.  ADJ = true: out[128 columns of A] = A^T Q.
+template <int BK, bool ADJ>
+__global__ void __launch_bounds__(256, 1) tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const Plan<BK> P(args.N);
+    uint64_t *full_a = reinterpret_cast<uint64_t *>(smem + P.off_bar);
+    uint64_t *empty_a = full_a + kStagesA;
+    uint64_t *full_c = empty_a + kStagesA;
+    uint64_t *empty_c = full_c + kBufs;
+    uint64_t *done = empty_c + kBufs;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = args.N;
+    const uint32_t tmem_cols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+
+    // K range of this CTA
+    const int64_t tile0 = (int64_t)blockIdx.x * kBM;            // output rows of this CTA
+    const int64_t kbeg = ADJ ? (int64_t)blockIdx.y * args.k_begin_stride : 0;
+    const int64_t kend = ADJ ? min(args.K, kbeg + args.k_begin_stride) : args.K;
+    const int nstages = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
+    const int64_t stage0 = kbeg / BK;                            // block-operand stage index base
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], 4); }
+        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], 5); mbar_init(&empty_c[b], 1); }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    bool ok = true;
+
+    auto fail = [&]() {
+        if (!*abort_flag) {
+            *abort_flag = 1;
+            atomicAdd(&args.st->timeouts, 1);
+            dev_fail(args.st, RPCA_ERR_TIMEOUT);
+        }
+        ok = false;
+    };
+
+    if (warp == 0) {
+        // ---------------- FP32 A producer (TMA) ----------------
+        if (lane == 0) {
+            for (int k = 0; k < nstages && ok; ++k) {
+                const int s = k % kStagesA;
+                if (k >= kStagesA && !mbar_wait(&empty_a[s], ((k / kStagesA) & 1) ^ 1, abort_flag)) { fail(); break; }
+                uint8_t *dst = smem + P.off_a32 + s * P.a32_bytes;
+                mbar_arrive_tx(&full_a[s], P.a32_bytes);
+                const int64_t kk = kbeg + (int64_t)k * BK;
+                if (!ADJ) {
+                    // boxes of 32 columns (k) x 128 rows, row tile0
+                    for (int b = 0; b < BK / 32; ++b)
+                        tma_load_2d(dst + b * (kBM * 128), &tmap, (int)(kk + 32 * b), (int)tile0, &full_a[s]);
+                } else {
+                    // boxes of 32 columns (tile0 + 32 b) x BK rows starting at row kk
+                    for (int b = 0; b < kBM / 32; ++b)
+                        tma_load_2d(dst + b * (BK * 128), &tmap, (int)(tile0 + 32 * b), (int)kk, &full_a[s]);
+                }
+            }
+        }
+    } else if (warp == 3) {
+        // ---------------- block operand producer (bulk copies) ----------------
+        if (lane == 0) {
+            for (int k = 0; k < nstages && ok; ++k) {
+                const int b = k % kBufs;
+                if (k >= kBufs && !mbar_wait(&empty_c[b], ((k / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+                uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
+                const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * 2 * N * BK;
+                mbar_arrive_tx(&full_c[b], 2 * P.b_bytes);
+                bulk_load(buf + 2 * P.abf_bytes, src, 2 * P.b_bytes, &full_c[b]);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_bf16(kBM, N);
+            for (int k = 0; k < nstages && ok; ++k) {
+                const int b = k % kBufs;
+                if (!mbar_wait(&full_c[b], (k / kBufs) & 1, abort_flag)) { fail(); break; }
+                tc_fence_after();
+                const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
+                const uint32_t a_hi = base, a_lo = base + P.abf_bytes;
+                const uint32_t b_hi = base + 2 * P.abf_bytes, b_lo = b_hi + P.b_bytes;
+                constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint32_t o = kk * 256;
+                    const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
+                    umma_bf16(tmem_base, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, acc0);
+                    umma_bf16(tmem_base, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), idesc, 1u);
+                    umma_bf16(tmem_base, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, 1u);
+                }
+                umma_commit(&empty_c[b]);
+            }
+            if (ok) umma_commit(done);
+        }
+    } else if (warp >= 4) {
+        // ---------------- converters, then epilogue ----------------
+        const int t = threadIdx.x - 128;                       // 0..127
+        for (int k = 0; k < nstages && ok; ++k) {
+            const int s = k % kStagesA, b = k % kBufs;
+            if (!mbar_wait(&full_a[s], (k / kStagesA) & 1, abort_flag)) { fail(); break; }
+            if (k >= kBufs && !mbar_wait(&empty_c[b], ((k / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+            const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
+            uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
+            uint8_t *dhi = buf, *dlo = buf + P.abf_bytes;
+            // core matrices: 16 (M) x BK/8 (K); 8 threads per core matrix (one row each)
+            constexpr int tasks = (kBM / 8) * (BK / 8) * 8;
+#pragma unroll 2
+            for (int id = t; id < tasks; id += 128) {
+                const int rr = id & 7, core = id >> 3;
+                const int ki = core % (BK / 8), mi = core / (BK / 8);
+                float x[8];
+                if (!ADJ) {
+                    // element (row r, col kcol) of a 128 x 32 box b: r*128 + ((kcol/4) ^ (r%8))*16 + (kcol%4)*4
+                    const int r = mi * 8 + rr;
+                    const int bx = ki >> 2, c0 = (ki & 3) * 2;              // two 16-byte chunks
+                    const uint8_t *row = src + bx * (kBM * 128) + r * 128;
+                    const float4 v0 = *reinterpret_cast<const float4 *>(row + ((c0 ^ (r & 7)) << 4));
+                    const float4 v1 = *reinterpret_cast<const float4 *>(row + (((c0 + 1) ^ (r & 7)) << 4));
+                    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                } else {
+                    // A^T: operand row = column j of A, K = row i of A; box bx holds columns 32bx..32bx+31
+                    const int j = mi * 8 + rr;
+                    const int bx = j >> 5, jc = j & 31;
+                    const uint8_t *box = src + bx * (BK * 128);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int i = ki * 8 + e;
+                        x[e] = *reinterpret_cast<const float *>(box + i * 128 + (((jc >> 2) ^ (i & 7)) << 4) +
+                                                                 (jc & 3) * 4);
+                    }
+                }
+                uint4 hi, lo;
+                split8(x, hi, lo);
+                const uint32_t off = (uint32_t)(mi * (BK / 8) + ki) * 128 + rr * 16;
+                *reinterpret_cast<uint4 *>(dhi + off) = hi;
+                *reinterpret_cast<uint4 *>(dlo + off) = lo;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty_a[s]);
+                mbar_arrive(&full_c[b]);
+            }
+        }
+        // epilogue: TMEM lanes 32*(warp%4) .. +31 hold output rows tile0 + that range
+        if (ok && nstages > 0) {
+            if (!mbar_wait(done, 0, abort_flag)) {
+                fail();
+            } else {
+                tc_fence_after();
+                const int q = warp & 3;
+                const int64_t row = tile0 + q * 32 + lane;
+                float *orow = args.out + (int64_t)blockIdx.y * args.split_stride + row * args.ldo;
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    if (row < args.out_rows) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (c0 + e < args.ncols_store) orow[c0 + e] = v[e];
+                    }
+                }
+            }
+        } else if (nstages == 0) {
+            // empty K range: the partial is zero
+            const int q = warp & 3;
+            const int64_t row = tile0 + q * 32 + lane;
+            if (row < args.out_rows) {
+                float *orow = args.out + (int64_t)blockIdx.y * args.split_stride + row * args.ldo;
+                for (int c = 0; c < args.ncols_store; ++c) orow[c] = 0.f;
+            }
+        }
+    }
+
+    // Drain: after an abort, let copies that were issued land before the CTA exits.
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        for (int s = 0; s < kStagesA; ++s) {
+            const long long t0 = clock64();
+            while (!mbar_try(&full_a[s], 0) && !mbar_try(&full_a[s], 1) && clock64() - t0 < kWaitCycles) {}
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block operand: FP32 P (rows x ld) -> per stage of BK rows, hi then lo, each
+// N x BK BF16 in K-major core matrices ((n/8) * (BK/8) + k/8) * 64 + (n%8) * 8 + k%8.
+// ---------------------------------------------------------------------------
+template <int BK>
+__global__ void __launch_bounds__(256)
+split_block_kernel(const float *__restrict__ P, int64_t rows, int ncols, int64_t ld, int N,
+                   __nv_bfloat16 *__restrict__ out, int64_t nstages) {
+    const int64_t chunks = nstages * (int64_t)(N / 8) * (BK / 8) * 8;     // 16-byte chunks per half
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(c & 7);
+        const int64_t core = c >> 3;
+        const int ki = (int)(core % (BK / 8));
+        const int64_t t2 = core / (BK / 8);
+        const int ni = (int)(t2 % (N / 8));
+        const int64_t s = t2 / (N / 8);
+        const int col = ni * 8 + rr;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t i = s * BK + ki * 8 + e;
+            x[e] = (i < rows && col < ncols) ? P[i * ld + col] : 0.f;
+        }
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        __nv_bfloat16 *base = out + s * 2 * (int64_t)N * BK;
+        const int64_t off = ((int64_t)(ni * (BK / 8) + ki) * 64 + rr * 8);
+        *reinterpret_cast<uint4 *>(base + off) = hi;
+        *reinterpret_cast<uint4 *>(base + (int64_t)N * BK + off) = lo;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap *map, const float *A, int64_t m, int64_t n, int64_t lda, uint32_t box_x, uint32_t box_y) {
+    auto enc = get_encode();
+    if (!enc) return RPCA_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
+    cuuint32_t box[2] = {box_x, box_y};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(A), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
+template <int BK, bool ADJ>
+int launch_pass(const CUtensorMap &map, const TcArgs &a, dim3 grid, cudaStream_t s) {
+    const Plan<BK> P(a.N);
+    const size_t smem = P.total + 1024;
+    auto kern = tc_pass_kernel<BK, ADJ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RPCA_ERR_CUDA;
+    kern<<<grid, 256, smem, s>>>(map, a);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+}  // namespace
+
+int tc_n(int lp) { return (int)round_up(lp, 16); }
+int tc_bk(int lp) { return tc_n(lp) <= 128 ? 64 : 32; }
+
+bool tc_supported(const float *A, int64_t lda, int lp) {
+    return tc_n(lp) <= 256 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && lda % 4 == 0;
+}
+
+size_t tc_split_bytes(int64_t rows, int lp) {
+    const int N = tc_n(lp), BK = tc_bk(lp);
+    return (size_t)cdiv(rows, BK) * 2 * N * BK * sizeof(__nv_bfloat16);
+}
+
+int tc_adjoint_splits(int64_t n, int64_t m, int lp) {
+    const int64_t tiles = cdiv(n, kBM);
+    const int64_t stages = cdiv(m, tc_bk(lp));
+    int64_t s = std::max<int64_t>(1, num_sms() / tiles);
+    return (int)std::min<int64_t>(s, std::max<int64_t>(1, stages / 4));
+}
+
+int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cudaStream_t s) {
+    const int N = tc_n(lp), BK = tc_bk(lp);
+    const int64_t nst = cdiv(rows, BK);
+    const int64_t chunks = nst * (N / 8) * (BK / 8) * 8;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(cdiv(chunks, 256), (int64_t)num_sms() * 8));
+    if (BK == 64)
+        split_block_kernel<64><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
+    else
+        split_block_kernel<32><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *xsplit, int lp,
+                    float *Y, DevStatus *st, cudaStream_t s) {
+    const int N = tc_n(lp), BK = tc_bk(lp);
+    CUtensorMap map;
+    RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
+    TcArgs a{xsplit, Y, m, lp, lp, N, 0, n, 0, st};
+    dim3 grid((unsigned)cdiv(m, kBM), 1, 1);
+    return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
+}
+
+int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *qsplit, int lp,
+                      float *part, int splits, DevStatus *st, cudaStream_t s) {
+    const int N = tc_n(lp), BK = tc_bk(lp);
+    CUtensorMap map;
+    RPCA_TRY(make_map(&map, A, m, n, lda, 32, (uint32_t)BK));
+    const int64_t per = round_up(cdiv(m, splits), BK);
+    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, st};
+    dim3 grid((unsigned)cdiv(n, kBM), (unsigned)splits, 1);
+    return BK == 64 ? launch_pass<64, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
+}
+
+}  // namespace rpca

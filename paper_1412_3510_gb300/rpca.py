@@ -149,3 +149,77 @@ def rpca_philox4x64_10(key0: int, key1: int, first: int, nblocks: int, device="c
 
 def rpca_launch_count() -> int:
     return int(L.load().rpca_launch_count())
+
+
+def rpca_resid_norm(A: torch.Tensor, U: torch.Tensor, S: torch.Tensor, V: torch.Tensor,
+                    raw: bool = False, iters: int = 20, seed: int = 0, ws: torch.Tensor | None = None,
+                    est: torch.Tensor | None = None, stream=None, sync: bool = True):
+    """Power-method estimate of ||A_c - U diag(S) V^T||_2 (Section 4), as a float (sync=True)
+    or as the 1-element float64 device tensor it is written to (sync=False)."""
+    _need_cuda(A, "A")
+    lda = _rowmajor_ld(A, "A")
+    m, n = A.shape
+    k = int(S.numel())
+    lib = L.load()
+    need = int(lib.rpca_resid_workspace_size(m, n, k))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_resid_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if est is None:
+        est = torch.empty(1, dtype=torch.float64, device=A.device)
+    ldu = _rowmajor_ld(U, "U") if k else k
+    ldv = _rowmajor_ld(V, "V") if k else k
+    code = lib.rpca_resid_norm(_ptr(A), m, n, lda, int(bool(raw)), _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                               k, int(iters), seed & ((1 << 64) - 1), _ptr(est), _ptr(ws), ws.numel(),
+                               _stream(stream))
+    _check(code, "rpca_resid_norm")
+    if sync:
+        _check(rpca_read_status(ws, stream), "rpca_resid_norm (device)")
+        return float(est.item())
+    return est
+
+
+def rpca_timing_enable(on: bool = True, reserve: int = 0) -> None:
+    """Turn stage timing on or off; `reserve` events are created up front."""
+    _check(L.load().rpca_timing_enable(max(int(bool(on)), int(reserve) if on else 0)), "rpca_timing_enable")
+
+
+def rpca_timing_reset() -> None:
+    _check(L.load().rpca_timing_reset(), "rpca_timing_reset")
+
+
+def rpca_timing_read(kind: int):
+    """(launches, total milliseconds) of the timed stage `kind` since the last reset."""
+    c = C.c_int64(0)
+    t = C.c_double(0.0)
+    _check(L.load().rpca_timing_read(int(kind), C.byref(c), C.byref(t)), "rpca_timing_read")
+    return int(c.value), float(t.value)
+
+
+def rpca_dense_pass(A: torch.Tensor, B: torch.Tensor, adjoint: bool = False, precision: str = "fp32",
+                    ws: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None,
+                    check: bool = True):
+    """One product without centring: A @ B (adjoint=False) or A.T @ B (adjoint=True).
+
+    B: (n or m) x w float32 CUDA, contiguous, w a multiple of 8 (<= 256)."""
+    _need_cuda(A, "A")
+    _need_cuda(B, "B")
+    lda = _rowmajor_ld(A, "A")
+    m, n = A.shape
+    B = B.contiguous()
+    w = int(B.shape[1])
+    lib = L.load()
+    need = int(lib.rpca_dense_pass_workspace_size(m, n, w, int(adjoint), L.PREC[precision]))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_dense_pass_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    rows = n if adjoint else m
+    C = torch.empty(rows, w, dtype=torch.float32, device=A.device) if out is None else out
+    code = lib.rpca_dense_pass(_ptr(A), m, n, lda, int(adjoint), _ptr(B), w, _ptr(C), L.PREC[precision],
+                               _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "rpca_dense_pass")
+    if check:
+        _check(rpca_read_status(ws, stream), "rpca_dense_pass (device)")
+    return C

@@ -262,4 +262,8 @@ WORKLOADS = {
                                    spectrum=lambda r: spectrum_pow15(r, 1236), seed=1236),
     "dense_200000x20000_k200": dict(m=200000, n=20000, k=200, l=210, its=2, raw=False,
                                     spectrum=lambda r: spectrum_exp50(r), seed=1237),
+    # a quarter-size version of the 100000 x 2000 workload (A = 200 MB, still larger
+    # than L2) for profiler captures that must stay small
+    "dense_25000x2000_k100": dict(m=25000, n=2000, k=100, l=102, its=2, raw=False,
+                                  spectrum=lambda r: spectrum_pow15(r, 1236), seed=1238),
 }

@@ -57,19 +57,21 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("m,n,k,l,its,raw", CASES)
-def test_dense_parity(m, n, k, l, its, raw):
+def test_dense_parity(m, n, k, l, its, raw, precision):
     sig = np.exp(-np.arange(1, min(m, n) + 1) / max(4.0, l / 2.0))
     A = S.haar_dense_np(m, n, sig, seed=m * 7 + n)
     if not raw:
         A = A + np.float32(0.3) * np.random.default_rng(m).standard_normal(n).astype(np.float32)[None, :]
-    _check_parity(A, k, l, its, raw, seed=m + n + k)
+    _check_parity(A, k, l, its, raw, seed=m + n + k, precision=precision)
 
 
-def test_dense_first_workload_full_size():
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_dense_first_workload_full_size(precision):
     w = S.WORKLOADS["dense_2000x1000_k10"]
     A = S.haar_dense_np(w["m"], w["n"], w["spectrum"](min(w["m"], w["n"])), w["seed"])
-    _check_parity(A, w["k"], w["l"], w["its"], w["raw"], seed=1)
+    _check_parity(A, w["k"], w["l"], w["its"], w["raw"], seed=1, precision=precision)
 
 
 def test_section6_examples_on_gpu():
