@@ -149,6 +149,33 @@ int rpca_dense_pass(const float *A, int64_t m, int64_t n, int64_t lda, int32_t a
                     int32_t w, float *C, int32_t precision, void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * rpca_dense_pass without a caller workspace (the paper has no counterpart:
+ * this is a deployment variant of rpca_dense_pass).
+ *
+ * For callers that cannot allocate device memory: code inside a framework
+ * that owns all device memory through its own pool, code on a latency-critical
+ * path that cannot take cudaMalloc's implicit synchronisation, code that must
+ * not grow its device footprint after start-up.  The caller passes A, B and C
+ * exactly as for rpca_dense_pass; the scratch comes from a fixed buffer of
+ * RPCA_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the library, which every
+ * device that loads the library holds until the process exits.
+ *  - Problems whose rpca_dense_pass_workspace_size exceeds that size are
+ *    rejected with RPCA_ERR_WORKSPACE before anything runs.
+ *  - The first call on a device looks up the buffer's device address (once
+ *    per device, with that device current); make that first call before any
+ *    CUDA stream capture.
+ *  - All calls share the one buffer and it keeps the previous call's
+ *    contents; each call clears the status word it needs on `stream` first.
+ *    Calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race on the buffer: serialise them.
+ *  - Device-side status is not readable by the caller (there is no workspace
+ *    pointer); host-side errors are returned as usual.
+ * ---------------------------------------------------------------------- */
+#define RPCA_NOALLOC_SCRATCH_BYTES (64u << 20)
+int rpca_dense_pass_noalloc(const float *A, int64_t m, int64_t n, int64_t lda, int32_t adjoint, const float *B,
+                            int32_t w, float *C, int32_t precision, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * The sketch's test matrix alone (Section 2; the step every call starts with).
  * Writes Omega (n x l, row-major, leading dimension ldo >= l, device): entry
  * (i, j) is element e = i*l + j of the stream in which Philox4x64-10 block b

@@ -17,6 +17,7 @@ RPCA_ERR_BREAKDOWN = -5
 RPCA_ERR_TIMEOUT = -6
 RPCA_ERR_UNSUPPORTED = -7
 RPCA_MAX_L = 224
+RPCA_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 PREC = {"fp32": 0, "bf16x3": 1}
 RENORM = {"cholqr": 0, "lu": 1}
@@ -44,6 +45,7 @@ SIGNATURES = [
                                   _P, _P, _SZ, _P]),
     ("rpca_dense_pass_workspace_size", _SZ, [_I64, _I64, _I32, _I32, _I32]),
     ("rpca_dense_pass", C.c_int, [_P, _I64, _I64, _I64, _I32, _P, _I32, _P, _I32, _P, _SZ, _P]),
+    ("rpca_dense_pass_noalloc", C.c_int, [_P, _I64, _I64, _I64, _I32, _P, _I32, _P, _I32, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
