@@ -7,13 +7,18 @@
 // block operand (X or Q) is split the same way, and three BF16 products
 // a_hi b_hi + a_hi b_lo + a_lo b_hi accumulate in FP32 in tensor memory.
 //
-// One CTA owns a 128-row tile of the output (rows of A for A X, columns of A
-// for A^T Q) and all N <= 256 output columns:
-//   warp 0       TMA loads of FP32 A tiles (128B-swizzled boxes), 3-stage ring
-//   warp 3       bulk copies of the pre-split BF16 block tiles
-//   warps 4..7   split each FP32 stage into BF16 hi/lo in the MMA's canonical
-//                K-major layout (transposing for A^T), then the epilogue
-//   warp 1       TMEM allocation; one lane issues the MMAs
+// Persistent kernel, one CTA per SM, looping over 128-row output tiles (rows
+// of A for A X; (column tile, K split) pairs for A^T Q), all N <= 256 output
+// columns per tile:
+//   warp 0       TMA loads of FP32 A stages (128B-swizzled 32-column boxes),
+//                3-stage ring
+//   warp 2       bulk copies of the pre-split BF16 block-operand stages
+//   warps 8..15  split each FP32 stage into BF16 hi/lo in the MMA's canonical
+//                K-major layout (transposing for A^T); the swizzle keeps these
+//                shared-memory reads free of bank conflicts
+//   warp 1       TMEM allocation (two accumulators); one lane issues the MMAs
+//   warps 4..7   epilogue: tcgen05.ld of one accumulator while the MMAs fill
+//                the other, FP32 stores
 // Every wait on an mbarrier is bounded; a wait that runs out records
 // RPCA_ERR_TIMEOUT in the status block and the CTA drains and exits.
 #include "internal.cuh"
@@ -120,19 +125,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) {
+    return *reinterpret_cast<uint32_t *>(&v);
 }
-// Split 8 floats into hi/lo BF16 octets.
+// Split 8 floats into hi/lo BF16 octets: hi = bf16(x), lo = bf16(x - hi).
 __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
-    __nv_bfloat16 h[8], l[8];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        h[e] = __float2bfloat16_rn(x[e]);
-        l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 hb = __float22bfloat162_rn(make_float2(x[2 * e], x[2 * e + 1]));
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __float22bfloat162_rn(make_float2(x[2 * e] - hf.x, x[2 * e + 1] - hf.y));
+        h[e] = bf2_bits(hb);
+        l[e] = bf2_bits(lb);
     }
-    hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-    lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).
@@ -154,20 +162,27 @@ struct Plan {
 
 struct TcArgs {
     const __nv_bfloat16 *bsplit;  // pre-split block operand: per stage [hi | lo], each N x BK
-    float *out;                   // output (+ blockIdx.y * split_stride)
+    float *out;                   // output (+ split * split_stride)
     int64_t out_rows;             // rows of the output that exist (m for A X, n for A^T Q)
     int64_t ldo;                  // leading dimension of out
     int ncols_store;              // columns to store (lp)
     int N;                        // MMA N (multiple of 16, <= 256)
-    int64_t k_begin_stride;       // K elements per split (adjoint), 0 for A X
+    int64_t per_split;            // K rows per split (A^T Q), K for A X
     int64_t K;                    // total K (n for A X, m for A^T Q)
     int64_t split_stride;         // elements between output partials
+    int row_tiles;                // 128-row output tiles
+    int ntiles;                   // row_tiles x splits
     DevStatus *st;
 };
 
-// ADJ = false: out[128 rows of A] = A X.  ADJ = true: out[128 columns of A] = A^T Q.
+constexpr int kThreads = 512;     // 16 warps
+constexpr int kConvWarps = 8;     // warps 8..15
+constexpr int kEpiWarp0 = 4;      // warps 4..7
+
+// ADJ = false: out[128 rows of A] = A X.  ADJ = true: out[128 columns of A] = A^T Q
+// over the rows of one split.  Persistent: CTA b takes tiles b, b + gridDim.x, ...
 template <int BK, bool ADJ>
-__global__ void __launch_bounds__(256, 1) tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
+__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const Plan<BK> P(args.N);
@@ -175,25 +190,20 @@ __global__ void __launch_bounds__(256, 1) tc_pass_kernel(const __grid_constant__
     uint64_t *empty_a = full_a + kStagesA;
     uint64_t *full_c = empty_a + kStagesA;
     uint64_t *empty_c = full_c + kBufs;
-    uint64_t *done = empty_c + kBufs;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *tm_full = empty_c + kBufs;
+    uint64_t *tm_empty = tm_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tm_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = args.N;
-    const uint32_t tmem_cols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-
-    // K range of this CTA
-    const int64_t tile0 = (int64_t)blockIdx.x * kBM;            // output rows of this CTA
-    const int64_t kbeg = ADJ ? (int64_t)blockIdx.y * args.k_begin_stride : 0;
-    const int64_t kend = ADJ ? min(args.K, kbeg + args.k_begin_stride) : args.K;
-    const int nstages = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
-    const int64_t stage0 = kbeg / BK;                            // block-operand stage index base
+    const uint32_t acc_cols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+    const uint32_t tmem_cols = 2 * acc_cols;                  // two accumulators
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], 4); }
-        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], 5); mbar_init(&empty_c[b], 1); }
-        mbar_init(done, 1);
+        for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
+        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], kConvWarps + 1); mbar_init(&empty_c[b], 1); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&tm_full[a], 1); mbar_init(&tm_empty[a], 4); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -217,153 +227,204 @@ __global__ void __launch_bounds__(256, 1) tc_pass_kernel(const __grid_constant__
         }
         ok = false;
     };
+    // tile -> (first output row, K range)
+    auto tile_info = [&](int t, int64_t &row0, int64_t &kbeg, int &nst) {
+        const int rt = t % args.row_tiles, sp = t / args.row_tiles;
+        row0 = (int64_t)rt * kBM;
+        kbeg = ADJ ? (int64_t)sp * args.per_split : 0;
+        const int64_t kend = ADJ ? min(args.K, kbeg + args.per_split) : args.K;
+        nst = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
+    };
 
     if (warp == 0) {
         // ---------------- FP32 A producer (TMA) ----------------
         if (lane == 0) {
-            for (int k = 0; k < nstages && ok; ++k) {
-                const int s = k % kStagesA;
-                if (k >= kStagesA && !mbar_wait(&empty_a[s], ((k / kStagesA) & 1) ^ 1, abort_flag)) { fail(); break; }
-                uint8_t *dst = smem + P.off_a32 + s * P.a32_bytes;
-                mbar_arrive_tx(&full_a[s], P.a32_bytes);
-                const int64_t kk = kbeg + (int64_t)k * BK;
-                if (!ADJ) {
-                    // boxes of 32 columns (k) x 128 rows, row tile0
-                    for (int b = 0; b < BK / 32; ++b)
-                        tma_load_2d(dst + b * (kBM * 128), &tmap, (int)(kk + 32 * b), (int)tile0, &full_a[s]);
-                } else {
-                    // boxes of 32 columns (tile0 + 32 b) x BK rows starting at row kk
-                    for (int b = 0; b < kBM / 32; ++b)
-                        tma_load_2d(dst + b * (BK * 128), &tmap, (int)(tile0 + 32 * b), (int)kk, &full_a[s]);
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+                int64_t row0, kbeg;
+                int nst;
+                tile_info(t, row0, kbeg, nst);
+                for (int k = 0; k < nst && ok; ++k, ++g) {
+                    const int s = g % kStagesA;
+                    if (g >= kStagesA && !mbar_wait(&empty_a[s], ((g / kStagesA) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    uint8_t *dst = smem + P.off_a32 + s * P.a32_bytes;
+                    mbar_arrive_tx(&full_a[s], P.a32_bytes);
+                    const int64_t kk = kbeg + (int64_t)k * BK;
+                    if (!ADJ) {
+                        for (int b = 0; b < BK / 32; ++b)
+                            tma_load_2d(dst + b * (kBM * 128), &tmap, (int)(kk + 32 * b), (int)row0, &full_a[s]);
+                    } else {
+                        for (int b = 0; b < kBM / 32; ++b)
+                            tma_load_2d(dst + b * (BK * 128), &tmap, (int)(row0 + 32 * b), (int)kk, &full_a[s]);
+                    }
                 }
             }
         }
-    } else if (warp == 3) {
+    } else if (warp == 2) {
         // ---------------- block operand producer (bulk copies) ----------------
         if (lane == 0) {
-            for (int k = 0; k < nstages && ok; ++k) {
-                const int b = k % kBufs;
-                if (k >= kBufs && !mbar_wait(&empty_c[b], ((k / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
-                uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
-                const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * 2 * N * BK;
-                mbar_arrive_tx(&full_c[b], 2 * P.b_bytes);
-                bulk_load(buf + 2 * P.abf_bytes, src, 2 * P.b_bytes, &full_c[b]);
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+                int64_t row0, kbeg;
+                int nst;
+                tile_info(t, row0, kbeg, nst);
+                const int64_t stage0 = kbeg / BK;
+                for (int k = 0; k < nst && ok; ++k, ++g) {
+                    const int b = g % kBufs;
+                    if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
+                    const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * 2 * N * BK;
+                    mbar_arrive_tx(&full_c[b], 2 * P.b_bytes);
+                    bulk_load(buf + 2 * P.abf_bytes, src, 2 * P.b_bytes, &full_c[b]);
+                }
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = instr_desc_bf16(kBM, N);
-            for (int k = 0; k < nstages && ok; ++k) {
-                const int b = k % kBufs;
-                if (!mbar_wait(&full_c[b], (k / kBufs) & 1, abort_flag)) { fail(); break; }
+            constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;
+            uint32_t g = 0, i = 0;
+            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++i) {
+                int64_t row0, kbeg;
+                int nst;
+                tile_info(t, row0, kbeg, nst);
+                const uint32_t acc = i & 1;
+                if (i >= 2 && !mbar_wait(&tm_empty[acc], ((i >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
                 tc_fence_after();
-                const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
-                const uint32_t a_hi = base, a_lo = base + P.abf_bytes;
-                const uint32_t b_hi = base + 2 * P.abf_bytes, b_lo = b_hi + P.b_bytes;
-                constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;
+                const uint32_t d = tmem_base + acc * acc_cols;
+                for (int k = 0; k < nst && ok; ++k, ++g) {
+                    const int b = g % kBufs;
+                    if (!mbar_wait(&full_c[b], (g / kBufs) & 1, abort_flag)) { fail(); break; }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
+                    const uint32_t a_hi = base, a_lo = base + P.abf_bytes;
+                    const uint32_t b_hi = base + 2 * P.abf_bytes, b_lo = b_hi + P.b_bytes;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint32_t o = kk * 256;
-                    const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
-                    umma_bf16(tmem_base, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, acc0);
-                    umma_bf16(tmem_base, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), idesc, 1u);
-                    umma_bf16(tmem_base, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, 1u);
-                }
-                umma_commit(&empty_c[b]);
-            }
-            if (ok) umma_commit(done);
-        }
-    } else if (warp >= 4) {
-        // ---------------- converters, then epilogue ----------------
-        const int t = threadIdx.x - 128;                       // 0..127
-        for (int k = 0; k < nstages && ok; ++k) {
-            const int s = k % kStagesA, b = k % kBufs;
-            if (!mbar_wait(&full_a[s], (k / kStagesA) & 1, abort_flag)) { fail(); break; }
-            if (k >= kBufs && !mbar_wait(&empty_c[b], ((k / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
-            const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
-            uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
-            uint8_t *dhi = buf, *dlo = buf + P.abf_bytes;
-            // core matrices: 16 (M) x BK/8 (K); 8 threads per core matrix (one row each)
-            constexpr int tasks = (kBM / 8) * (BK / 8) * 8;
-#pragma unroll 2
-            for (int id = t; id < tasks; id += 128) {
-                const int rr = id & 7, core = id >> 3;
-                const int ki = core % (BK / 8), mi = core / (BK / 8);
-                float x[8];
-                if (!ADJ) {
-                    // element (row r, col kcol) of a 128 x 32 box b: r*128 + ((kcol/4) ^ (r%8))*16 + (kcol%4)*4
-                    const int r = mi * 8 + rr;
-                    const int bx = ki >> 2, c0 = (ki & 3) * 2;              // two 16-byte chunks
-                    const uint8_t *row = src + bx * (kBM * 128) + r * 128;
-                    const float4 v0 = *reinterpret_cast<const float4 *>(row + ((c0 ^ (r & 7)) << 4));
-                    const float4 v1 = *reinterpret_cast<const float4 *>(row + (((c0 + 1) ^ (r & 7)) << 4));
-                    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-                    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-                } else {
-                    // A^T: operand row = column j of A, K = row i of A; box bx holds columns 32bx..32bx+31
-                    const int j = mi * 8 + rr;
-                    const int bx = j >> 5, jc = j & 31;
-                    const uint8_t *box = src + bx * (BK * 128);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int i = ki * 8 + e;
-                        x[e] = *reinterpret_cast<const float *>(box + i * 128 + (((jc >> 2) ^ (i & 7)) << 4) +
-                                                                 (jc & 3) * 4);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t o = kk * 256;
+                        const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
+                        umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, acc0);
+                        umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), idesc, 1u);
+                        umma_bf16(d, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, 1u);
                     }
+                    umma_commit(&empty_c[b]);
                 }
-                uint4 hi, lo;
-                split8(x, hi, lo);
-                const uint32_t off = (uint32_t)(mi * (BK / 8) + ki) * 128 + rr * 16;
-                *reinterpret_cast<uint4 *>(dhi + off) = hi;
-                *reinterpret_cast<uint4 *>(dlo + off) = lo;
-            }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&empty_a[s]);
-                mbar_arrive(&full_c[b]);
+                if (ok) umma_commit(&tm_full[acc]);
             }
         }
-        // epilogue: TMEM lanes 32*(warp%4) .. +31 hold output rows tile0 + that range
-        if (ok && nstages > 0) {
-            if (!mbar_wait(done, 0, abort_flag)) {
-                fail();
-            } else {
-                tc_fence_after();
-                const int q = warp & 3;
-                const int64_t row = tile0 + q * 32 + lane;
-                float *orow = args.out + (int64_t)blockIdx.y * args.split_stride + row * args.ldo;
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (row < args.out_rows) {
+    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
+        // ---------------- epilogue: TMEM lanes 32*(warp%4)..+31 ----------------
+        const int q = warp & 3;
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++i) {
+            int64_t row0, kbeg;
+            int nst;
+            tile_info(t, row0, kbeg, nst);
+            const uint32_t acc = i & 1;
+            if (!mbar_wait(&tm_full[acc], (i >> 1) & 1, abort_flag)) { fail(); break; }
+            tc_fence_after();
+            const int sp = t / args.row_tiles;
+            const int64_t row = row0 + q * 32 + lane;
+            float *orow = args.out + (int64_t)sp * args.split_stride + row * args.ldo;
+            const bool live = row < args.out_rows;
+            const bool vec = ((reinterpret_cast<uintptr_t>(args.out) & 15u) == 0) && (args.ldo % 4 == 0) &&
+                             (args.split_stride % 4 == 0);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16];
+                if (nst > 0) {
+                    tmem_ld16(tmem_base + acc * acc_cols + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                }
+                if (live) {
+                    if (vec && c0 + 16 <= args.ncols_store) {
+#pragma unroll
+                        for (int e = 0; e < 16; e += 4)
+                            *reinterpret_cast<float4 *>(orow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                    } else {
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
                             if (c0 + e < args.ncols_store) orow[c0 + e] = v[e];
                     }
                 }
             }
-        } else if (nstages == 0) {
-            // empty K range: the partial is zero
-            const int q = warp & 3;
-            const int64_t row = tile0 + q * 32 + lane;
-            if (row < args.out_rows) {
-                float *orow = args.out + (int64_t)blockIdx.y * args.split_stride + row * args.ldo;
-                for (int c = 0; c < args.ncols_store; ++c) orow[c] = 0.f;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tm_empty[acc]);
+        }
+    } else if (warp >= 16 - kConvWarps) {
+        // ---------------- converters ----------------
+        const int t0 = threadIdx.x - (16 - kConvWarps) * 32;      // 0..255
+        constexpr int nthr = kConvWarps * 32;
+        uint32_t g = 0;
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+            int64_t row0, kbeg;
+            int nst;
+            tile_info(t, row0, kbeg, nst);
+            for (int k = 0; k < nst && ok; ++k, ++g) {
+                const int s = g % kStagesA, b = g % kBufs;
+                if (!mbar_wait(&full_a[s], (g / kStagesA) & 1, abort_flag)) { fail(); break; }
+                if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+                const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
+                uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
+                uint8_t *dhi = buf, *dlo = buf + P.abf_bytes;
+                // core matrices 16 (M) x BK/8 (K); 8 threads per core matrix (one row each)
+                constexpr int tasks = (kBM / 8) * (BK / 8) * 8;
+#pragma unroll
+                for (int id = t0; id < tasks; id += nthr) {
+                    const int rr = id & 7, core = id >> 3;
+                    int mi, ki;
+                    float x[8];
+                    if (!ADJ) {
+                        ki = core % (BK / 8);
+                        mi = core / (BK / 8);
+                        // element (r, kc) of a 128 x 32 box: r*128 + ((kc/4) ^ (r%8))*16 + (kc%4)*4
+                        const int r = mi * 8 + rr;
+                        const int bx = ki >> 2, c0 = (ki & 3) * 2;
+                        const uint8_t *row = src + bx * (kBM * 128) + r * 128;
+                        const float4 v0 = *reinterpret_cast<const float4 *>(row + ((c0 ^ (r & 7)) << 4));
+                        const float4 v1 = *reinterpret_cast<const float4 *>(row + (((c0 + 1) ^ (r & 7)) << 4));
+                        x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+                        x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+                    } else {
+                        // mi fastest, so that the four core matrices of a warp sit in distinct bank groups
+                        mi = core % (kBM / 8);
+                        ki = core / (kBM / 8);
+                        const int j = mi * 8 + rr;
+                        const int bx = j >> 5, jc = j & 31;
+                        const uint8_t *box = src + bx * (BK * 128);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int ii = ki * 8 + e;
+                            x[e] = *reinterpret_cast<const float *>(box + ii * 128 + (((jc >> 2) ^ (ii & 7)) << 4) +
+                                                                     (jc & 3) * 4);
+                        }
+                    }
+                    uint4 hi, lo;
+                    split8(x, hi, lo);
+                    const uint32_t off = (uint32_t)(mi * (BK / 8) + ki) * 128 + rr * 16;
+                    *reinterpret_cast<uint4 *>(dhi + off) = hi;
+                    *reinterpret_cast<uint4 *>(dlo + off) = lo;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&empty_a[s]);
+                    mbar_arrive(&full_c[b]);
+                }
             }
         }
     }
 
-    // Drain: after an abort, let copies that were issued land before the CTA exits.
+    // Drain: after an abort, give copies that were issued time to land.
     __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (*abort_flag && threadIdx.x == 0) {
-        for (int s = 0; s < kStagesA; ++s) {
-            const long long t0 = clock64();
-            while (!mbar_try(&full_a[s], 0) && !mbar_try(&full_a[s], 1) && clock64() - t0 < kWaitCycles) {}
-        }
+        const long long t0 = clock64();
+        while (clock64() - t0 < kWaitCycles / 100) {}
     }
     __syncthreads();
     if (warp == 1) {
@@ -439,7 +500,7 @@ int launch_pass(const CUtensorMap &map, const TcArgs &a, dim3 grid, cudaStream_t
     auto kern = tc_pass_kernel<BK, ADJ>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RPCA_ERR_CUDA;
-    kern<<<grid, 256, smem, s>>>(map, a);
+    kern<<<grid, kThreads, smem, s>>>(map, a);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
@@ -459,6 +520,7 @@ size_t tc_split_bytes(int64_t rows, int lp) {
 }
 
 int tc_adjoint_splits(int64_t n, int64_t m, int lp) {
+    // enough (column tile, split) work items to give every SM about one
     const int64_t tiles = cdiv(n, kBM);
     const int64_t stages = cdiv(m, tc_bk(lp));
     int64_t s = std::max<int64_t>(1, num_sms() / tiles);
@@ -483,8 +545,9 @@ int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __n
     const int N = tc_n(lp), BK = tc_bk(lp);
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
-    TcArgs a{xsplit, Y, m, lp, lp, N, 0, n, 0, st};
-    dim3 grid((unsigned)cdiv(m, kBM), 1, 1);
+    const int tiles = (int)cdiv(m, kBM);
+    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st};
+    dim3 grid((unsigned)std::min(tiles, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
 }
 
@@ -494,8 +557,9 @@ int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const _
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, (uint32_t)BK));
     const int64_t per = round_up(cdiv(m, splits), BK);
-    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, st};
-    dim3 grid((unsigned)cdiv(n, kBM), (unsigned)splits, 1);
+    const int rt = (int)cdiv(n, kBM);
+    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st};
+    dim3 grid((unsigned)std::min(rt * splits, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
 }
 
