@@ -287,7 +287,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     rp.rpca_timing_reset()
-    rp.rpca_timing_enable(True, reserve=2 * (2 * its + 3) * args.steps + 64)
+    rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
     launches0 = rp.rpca_launch_count()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -312,6 +312,8 @@ def main():
     n_apply, t_apply = rp.rpca_timing_read(0)
     n_adj, t_adj = rp.rpca_timing_read(1)
     n_svd, t_svd = rp.rpca_timing_read(3)
+    extra = {name: rp.rpca_timing_read(kind)[1] / args.steps
+             for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
     rp.rpca_timing_reset()
 
     # roofline of the dominant kernel (the passes over A)
@@ -395,8 +397,8 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "gbs_per_pass": gbs_per_pass,
         "passes_per_step": passes / args.steps,
-        "stage_ms_per_step": {"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,
-                              "small_svd": t_svd / args.steps},
+        "stage_ms_per_step": dict({"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,
+                                   "small_svd": t_svd / args.steps}, **extra),
         "accuracy": {"resid_est": est, "sigma_k1": sk1, "resid_over_sigma_k1": est / sk1,
                      "resid_ok": bool(est <= 1.1 * sk1), "status": status, "shifts": block["shifts"],
                      "jacobi_sweeps": block["jacobi_sweeps"]},

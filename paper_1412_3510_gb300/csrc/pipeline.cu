@@ -107,9 +107,16 @@ int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int sp
     float *part = c.at<float>(L.part);
     double *G = c.at<double>(L.G);
     float *rinv = c.at<float>(L.rinv);
-    RPCA_TRY(launch_sgemm(true, lp, lp, rows, in, lp, in, lp, part, lp, splits, (int64_t)lp * lp, c.s));
-    RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s));
-    RPCA_TRY(launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s));
+    {
+        TimedScope ts(kTimeGram, c.s);
+        RPCA_TRY(launch_sgemm(true, lp, lp, rows, in, lp, in, lp, part, lp, splits, (int64_t)lp * lp, c.s));
+        RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s));
+    }
+    {
+        TimedScope ts(kTimeChol, c.s);
+        RPCA_TRY(launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s));
+    }
+    TimedScope ts(kTimeTrsm, c.s);
     RPCA_TRY(launch_sgemm(false, rows, lp, lp, in, lp, rinv, lp, out, lp, 1, 0, c.s));
     return RPCA_OK;
 }
@@ -119,6 +126,7 @@ int renorm_m(const Ctx &c, bool raw, bool final_) {
     const Layout &L = c.L;
     float *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
     if (!raw) {
+        TimedScope ts(kTimeCentre, c.s);
         int nch = 0;
         RPCA_TRY(launch_colsum_partial(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), &nch, c.s));
         RPCA_TRY(launch_center(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), nch, c.s));
@@ -207,6 +215,7 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     }
 
     // V = Q2 Z_k, signs, U = Q W_k (Eq. i4)
+    TimedScope ts_lift(kTimeLift, s);
     RPCA_TRY(launch_sgemm(false, L.n, L.k, lp, x1, lp, zk, L.kp, V, ldv, 1, 0, s));
     RPCA_TRY(launch_sign_fix(V, L.n, ldv, L.k, wk, lp, L.kp, sig, S, s));
     RPCA_TRY(launch_sgemm(false, L.m, L.k, lp, y1, lp, wk, L.kp, U, ldu, 1, 0, s));

@@ -55,37 +55,50 @@ colsum_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld, float *__r
     }
 }
 
-// Y[r][c] -= mean_c (c < l), Y[r][c] = 0 (l <= c < ld); mean from the partials (FP64 sum).
+// Y[r][c] -= mean_c (c < l), Y[r][c] = 0 (l <= c < ld); mean from the partials
+// (compensated FP32 sum, recomputed by every CTA).
 __global__ void __launch_bounds__(256)
 center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
               const float *__restrict__ part, int nchunks) {
     __shared__ float mu[RPCA_MAX_L];
-    for (int c = threadIdx.x; c < l; c += blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < nchunks; ++q) s += (double)part[(int64_t)q * l + c];
-        mu[c] = (float)(s / (double)rows);
+    const int tflat = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int c = tflat; c < l; c += blockDim.x * blockDim.y) {
+        float s = 0.f, comp = 0.f;
+        for (int q = 0; q < nchunks; ++q) {
+            const float y = part[(int64_t)q * l + c] - comp;
+            const float t = s + y;
+            comp = (t - s) - y;
+            s = t;
+        }
+        mu[c] = s / (float)rows;
     }
     __syncthreads();
-    const int64_t total = rows * ld;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % ld);
-        Y[e] = (c < l) ? Y[e] - mu[c] : 0.f;
+    // blockDim = (32, 8): threadIdx.x walks the columns of a row, threadIdx.y the rows
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; r < rows; r += (int64_t)gridDim.x * blockDim.y) {
+        float *y = Y + r * ld;
+        for (int c = threadIdx.x; c < ld; c += blockDim.x) y[c] = (c < l) ? y[c] - mu[c] : 0.f;
     }
 }
 
-// G[a][b] = sum_s part[s][a][b] in FP64 (a, b < l).
+// G[a][b] = sum_s part[s][a][b] (a, b < l), compensated (Kahan) FP32 sum: the
+// result carries FP32-level relative error, as the FP32 Cholesky needs; GB300's
+// FP64 adds run at 1/64 of the FP32 rate.
 __global__ void __launch_bounds__(256)
 gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G) {
     const int64_t total = (int64_t)l * l;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int a = (int)(e / l), b = (int)(e % l);
-        double s = 0.0;
+        float s = 0.f, comp = 0.f;
         const float *p = part + (int64_t)a * lp + b;
         const int64_t stride = (int64_t)lp * lp;
-        for (int q = 0; q < splits; ++q) s += (double)p[q * stride];
-        G[e] = s;
+        for (int q = 0; q < splits; ++q) {
+            const float y = p[q * stride] - comp;
+            const float t = s + y;
+            comp = (t - s) - y;
+            s = t;
+        }
+        G[e] = (double)s;
     }
 }
 
@@ -165,8 +178,8 @@ int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value,
 
 int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, int nchunks,
                   cudaStream_t s) {
-    const int64_t grid = std::min<int64_t>(cdiv(rows * ld, 256), (int64_t)num_sms() * 4);
-    center_kernel<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(Y, rows, l, ld, part, nchunks);
+    const int64_t grid = std::min<int64_t>(cdiv(rows, 8), (int64_t)num_sms() * 4);
+    center_kernel<<<(unsigned)std::max<int64_t>(grid, 1), dim3(32, 8), 0, s>>>(Y, rows, l, ld, part, nchunks);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

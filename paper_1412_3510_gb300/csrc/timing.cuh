@@ -5,7 +5,10 @@
 
 namespace rpca {
 
-enum TimedKind { kTimeApply = 0, kTimeAdjoint = 1, kTimeRenorm = 2, kTimeSmallSvd = 3, kTimeResid = 4 };
+enum TimedKind {
+    kTimeApply = 0, kTimeAdjoint = 1, kTimeRenorm = 2, kTimeSmallSvd = 3, kTimeResid = 4,
+    kTimeGram = 5, kTimeChol = 6, kTimeTrsm = 7, kTimeCentre = 8, kTimeLift = 9
+};
 
 bool timing_on();
 
