@@ -124,10 +124,26 @@ def make_workload(name, device, rank):
     import numpy as np
     import synth
     w = dict(synth.WORKLOADS[name])
+    if w.get("kind") == "csr":
+        import torch
+        rp_, ci, va = synth.powerlaw_csr(w["m"], w["n"], w["nnz"], w["exponent"], w["rank"], w["seed"])
+        A = tuple(torch.from_numpy(x).to(device) for x in (rp_, ci, va))
+        return w, A, None
     r = min(w["m"], w["n"])
     sigma = w["spectrum"](r)
     A = synth.haar_dense_torch(w["m"], w["n"], sigma, w["seed"], device=device)
     return w, A, np.asarray(sigma)
+
+
+def sigma_k1_csr(A, shape, k):
+    """sigma_{k+1} of a sparse A by an independent randomized SVD (torch.svd_lowrank,
+    q = k + 30, 30 power iterations) -- measurement only."""
+    import torch
+    rp_, ci, va = A
+    S = torch.sparse_csr_tensor(rp_.long(), ci.long(), va, size=shape).to_sparse_coo()
+    g = torch.manual_seed(5)
+    _, s, _ = torch.svd_lowrank(S, q=k + 30, niter=30)
+    return float(s[k].item())
 
 
 def sigma_k1_reference(A, k, raw):
@@ -177,6 +193,13 @@ def oracle_sample(A_host, w, rows):
     return time.perf_counter() - t
 
 
+def csr_host(w):
+    import scipy.sparse as sp
+    import synth
+    rp_, ci, va = synth.powerlaw_csr(w["m"], w["n"], w["nnz"], w["exponent"], w["rank"], w["seed"])
+    return sp.csr_matrix((va, ci, rp_), shape=(w["m"], w["n"]))
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -195,7 +218,12 @@ def run_reference(args):
     r = min(w["m"], w["n"])
     # size each step's row sample so that warmup + steps take about ref_budget seconds
     probe_rows = max(w["l"] + 1, min(w["m"], 4000))
-    A = synth.haar_dense_np(min(w["m"], max(probe_rows, int(args.ref_rows))), w["n"], w["spectrum"](r), w["seed"])
+    if w.get("kind") == "csr":
+        A = csr_host(w)
+        probe_rows = max(w["l"] + 1, min(w["m"], 100000))
+    else:
+        A = synth.haar_dense_np(min(w["m"], max(probe_rows, int(args.ref_rows))), w["n"], w["spectrum"](r),
+                                w["seed"])
     t_probe = oracle_sample(A, w, probe_rows)
     per_row = t_probe / probe_rows
     rows = int(args.ref_budget / max(args.steps + args.warmup, 1) / max(per_row, 1e-9))
@@ -210,9 +238,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"],
-                   "its": w["its"], "raw": w["raw"]},
+                   "its": w["its"], "raw": w["raw"], "format": w.get("kind", "dense")},
         "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
-                         "sample": f"FP64 numpy oracle on the first {rows} of {w['m']} rows, time scaled by m"},
+                         "sample": f"FP64 numpy/scipy oracle on the first {rows} of {w['m']} rows, time scaled by m"},
         "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -263,16 +291,31 @@ def main():
 
     w, A, sigma = make_workload(args.workload, dev, rank)
     m, n, k, l, its, raw = w["m"], w["n"], w["k"], w["l"], w["its"], w["raw"]
+    csr = w.get("kind") == "csr"
+    if csr:
+        args.precision = "fp32"          # the sparse products are SIMT gathers
     opts = rp.make_opts(k, l, its, raw, seed=1 + rank, precision=args.precision)
-    ws = rp.workspace(rp.rpca_dense_workspace_size(m, n, opts), dev)
+    from paper_1412_3510_gb300 import _lib as LIB
+    import ctypes
+    if csr:
+        need = LIB.load().rpca_csr_workspace_size(m, n, w["nnz"], ctypes.byref(opts))
+    else:
+        need = rp.rpca_dense_workspace_size(m, n, opts)
+    ws = rp.workspace(need, dev)
     U = torch.empty(m, k, device=dev)
     S = torch.empty(k, device=dev)
     V = torch.empty(n, k, device=dev)
     stream = torch.cuda.current_stream()
 
+    def run(Ain):
+        if csr:
+            rp.rpca_csr(*Ain, (m, n), k, l, its=its, raw=raw, seed=1 + rank, ws=ws, out=(U, S, V), check=False)
+        else:
+            rp.rpca_dense(Ain, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
+                          out=(U, S, V), check=False)
+
     def step():
-        rp.rpca_dense(A, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
-                      out=(U, S, V), check=False)
+        run(A)
 
     for _ in range(args.warmup):
         step()
@@ -280,8 +323,12 @@ def main():
     block = rp.read_status_block(ws)
 
     # accuracy check outside the timed region: resid <= 1.1 sigma_{k+1}
-    est = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
-    sk1 = sigma_k1_reference(A, k, raw)
+    if csr:
+        est = rp.rpca_resid_norm_csr(*A, (m, n), U, S, V, raw=raw, iters=args.resid_iters, seed=7)
+        sk1 = sigma_k1_csr(A, (m, n), k)
+    else:
+        est = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
+        sk1 = sigma_k1_reference(A, k, raw)
 
     # timed region
     sampler = ClockSampler(local)
@@ -318,14 +365,25 @@ def main():
 
     # roofline of the dominant kernel (the passes over A)
     pk = peaks()
-    a_bytes = 4.0 * m * n
+    if csr:
+        nnz = w["nnz"]
+        a_bytes = 8.0 * nnz + 2.0 * (m + n + 2)      # values + indices, averaged over the A and A^T passes
+        pass_flops = 2.0 * nnz * l
+    else:
+        a_bytes = 4.0 * m * n
+        pass_flops = 2.0 * m * n * l
     pass_bytes = a_bytes + 4.0 * (m + n) * l        # A + the block read + the block written
-    pass_flops = 2.0 * m * n * l
     passes = n_apply + n_adj
     avg_pass_ms = (t_apply + t_adj) / max(passes, 1)
     gbs_per_pass = pass_bytes / (avg_pass_ms * 1e-3) / 1e9
     kernel_files = ["paper_1412_3510_gb300/csrc/gemm_simt.cu"]
-    if args.precision == "fp32":
+    if csr:
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": gbs_per_pass, "peak": peak, "unit": "GB/s", "frac": gbs_per_pass / peak,
+                "peak_source": pk["source"], "kernel": "spmm kernels (A and A^T passes)"}
+        key = "spmm_csr"
+        kernel_files = ["paper_1412_3510_gb300/csrc/csr.cu"]
+    elif args.precision == "fp32":
         peak = SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = pass_flops / (avg_pass_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -337,29 +395,32 @@ def main():
         roof = {"bound": "hbm", "achieved": gbs_per_pass, "peak": peak, "unit": "GB/s", "frac": gbs_per_pass / peak,
                 "peak_source": pk["source"], "kernel": "tcgen05 pass kernels"}
         key = "tc_pass_bf16x3"
+        kernel_files = ["paper_1412_3510_gb300/csrc/tc_gemm.cu"]
     sha = source_sha(kernel_files)
     roof["traffic"] = traffic_from_profiles(key, sha)
 
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        A_host = A.cpu().pin_memory()
+        parts = A if csr else (A,)
+        hosts = [x.cpu().pin_memory() for x in parts]
+        devs = [torch.empty_like(x) for x in parts]
         U_h = torch.empty(m, k).pin_memory()
         S_h = torch.empty(k).pin_memory()
         V_h = torch.empty(n, k).pin_memory()
-        A_dev = torch.empty_like(A)
+
+        def upload():
+            for d, h in zip(devs, hosts):
+                d.copy_(h, non_blocking=True)
+            return tuple(devs) if csr else devs[0]
         for _ in range(2):
-            A_dev.copy_(A_host, non_blocking=True)
-            rp.rpca_dense(A_dev, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
-                          out=(U, S, V), check=False)
+            run(upload())
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
-            A_dev.copy_(A_host, non_blocking=True)
-            rp.rpca_dense(A_dev, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
-                          out=(U, S, V), check=False)
+            run(upload())
             U_h.copy_(U, non_blocking=True)
             S_h.copy_(S, non_blocking=True)
             V_h.copy_(V, non_blocking=True)
@@ -371,13 +432,19 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
         e2e = {"value": world * args.e2e_steps / (e2e_ms / 1e3), "unit": "PCA/s",
-               "h2d_bytes_per_step": int(A.numel() * 4), "d2h_bytes_per_step": int((m * k + k + n * k) * 4)}
-        del A_host, A_dev
+               "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in parts)),
+               "d2h_bytes_per_step": int((m * k + k + n * k) * 4)}
+        del hosts, devs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        A_host = A[: min(m, args.ref_rows)].cpu().numpy()
-        rows = A_host.shape[0]
+        if csr:
+            import scipy.sparse as sp
+            A_host = sp.csr_matrix((A[2].cpu().numpy(), A[1].cpu().numpy(), A[0].cpu().numpy()), shape=(m, n))
+            rows = min(m, 200000)
+        else:
+            A_host = A[: min(m, args.ref_rows)].cpu().numpy()
+            rows = A_host.shape[0]
         t = oracle_sample(A_host, w, rows)
         cpu = {"value": 1.0 / (t * m / rows), "unit": "PCA/s", "cores": cores(), "kind": "oracle",
                "sample": f"one FP64 numpy oracle PCA on the first {rows} of {m} rows "
@@ -392,6 +459,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "its": its, "raw": raw,
+                   "format": "csr" if csr else "dense", "nnz": w.get("nnz"),
                    "precision": args.precision, "renorm": "cholqr",
                    "A_bytes": int(a_bytes), "l2": "A (%.0f MB) is larger than L2 (129 MB); no flush" % (a_bytes / 1e6),
                    "parallelism": f"replicas x{world}"},

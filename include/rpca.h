@@ -110,9 +110,12 @@ int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, const rpca_opt
  * that the same code serves dense and sparse A).
  *
  * row_ptr: m + 1 int32 (device), row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz.
- * col_idx: nnz int32 in [0, n) (device).  val: nnz FP32 (device).
- * Duplicate column indices within a row are summed.
- * Other arguments as rpca_dense.
+ * col_idx: nnz int32 in [0, n) (device), any order within a row.  val: nnz FP32 (device).
+ * Duplicate column indices within a row are summed.  A violation of these
+ * rules is reported as RPCA_ERR_INVALID_ARG in the device status; out-of-range
+ * entries are skipped, never read through.  A^T is built once per call (stable
+ * radix sort by column, in the workspace); every result is deterministic.
+ * Other arguments as rpca_dense; precision applies to dense A only.
  * ---------------------------------------------------------------------- */
 size_t rpca_csr_workspace_size(int64_t m, int64_t n, int64_t nnz, const rpca_opts *o);
 int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
@@ -133,6 +136,13 @@ int rpca_resid_norm(const float *A, int64_t m, int64_t n, int64_t lda, int32_t r
                     const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv,
                     int32_t k, int32_t iters, uint64_t seed, double *est,
                     void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* The same estimate for A in CSR form (arguments as rpca_csr and rpca_resid_norm). */
+size_t rpca_resid_csr_workspace_size(int64_t m, int64_t n, int64_t nnz, int32_t k);
+int rpca_resid_norm_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                        const float *val, int32_t raw, const float *U, int64_t ldu, const float *S,
+                        const float *V, int64_t ldv, int32_t k, int32_t iters, uint64_t seed, double *est,
+                        void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * One product of the method alone (the sketch's A Omega, either half of a

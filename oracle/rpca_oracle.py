@@ -131,9 +131,18 @@ def gaussian_omega(n: int, l: int, seed: int, stream: int = 0) -> np.ndarray:
 # implicit centring (Section 5)
 # ---------------------------------------------------------------------------
 
-def column_means(A: np.ndarray) -> np.ndarray:
+def _as_f64(A):
+    """A widened to FP64; a scipy sparse matrix stays sparse (Section 5: the same code
+    serves dense and sparse A, through products only)."""
+    import scipy.sparse as sp
+    if sp.issparse(A):
+        return sp.csr_matrix(A, dtype=np.float64)
+    return np.asarray(A, dtype=np.float64)
+
+
+def column_means(A) -> np.ndarray:
     """c: the 1 x n vector of the means of the columns of A (Section 5)."""
-    return np.asarray(A, dtype=np.float64).mean(axis=0)
+    return np.asarray(_as_f64(A).mean(axis=0), dtype=np.float64).ravel()
 
 
 def apply_centred(A, X, c):
@@ -141,7 +150,7 @@ def apply_centred(A, X, c):
 
     ``c`` is None when the matrix is used raw (no centring).
     """
-    Y = A @ X
+    Y = np.asarray(A @ X)
     if c is not None:
         Y = Y - np.ones((A.shape[0], 1)) @ (c[None, :] @ X)
     return Y
@@ -149,7 +158,7 @@ def apply_centred(A, X, c):
 
 def apply_centred_adjoint(A, Y, c):
     """A_c^* Y = (Y'*A)' - c' * (ones(1,m)*Y): the adjoint applied through A itself."""
-    X = (Y.T @ A).T
+    X = np.asarray(Y.T @ A).T
     if c is not None:
         X = X - c[:, None] @ (np.ones((1, A.shape[0])) @ Y)
     return X
@@ -345,7 +354,7 @@ def rpca(A, k: int, l: int | None = None, its: int = 2, raw: bool = False,
     5. Keep the leading k triplets; fix signs as in ``normalise_signs``.
     Returns (U m x k, S k, V n x k), all FP64.
     """
-    A = np.asarray(A, dtype=np.float64)
+    A = _as_f64(A)
     m, n = A.shape
     if l is None:
         l = k + 2
@@ -382,7 +391,7 @@ def resid_power(A, U, S, V, raw: bool = False, iters: int = 20, seed: int = 0):
     x = z / |z|.  Returns sqrt(lambda) after ``iters`` iterations; since
     |E^T E x| <= ||E||^2 for unit x the estimate never exceeds ||E||.
     """
-    A = np.asarray(A, dtype=np.float64)
+    A = _as_f64(A)
     U = np.asarray(U, dtype=np.float64)
     S = np.asarray(S, dtype=np.float64)
     V = np.asarray(V, dtype=np.float64)
@@ -402,7 +411,8 @@ def resid_power(A, U, S, V, raw: bool = False, iters: int = 20, seed: int = 0):
 
 def resid_exact(A, U, S, V, raw: bool = False) -> float:
     """||A_c - U diag(S) V^T||_2 from the full Jacobi SVD of the dense residual (small sizes)."""
-    A = np.asarray(A, dtype=np.float64)
+    A = _as_f64(A)
+    A = A.toarray() if hasattr(A, "toarray") else A
     E = A - (0.0 if raw else column_means(A)[None, :]) - (np.asarray(U) * np.asarray(S)[None, :]) @ np.asarray(V).T
     return float(jacobi_svd(E)[1][0])
 
@@ -413,7 +423,8 @@ def exact_singular_values(A, raw: bool = False) -> np.ndarray:
     Used as ground truth for sigma_{k+1}.  Squaring costs relative accuracy
     u * (sigma_1 / sigma_j)^2 in FP64, i.e. 1e-10 at sigma_j = 1e-3 sigma_1.
     """
-    A = np.asarray(A, dtype=np.float64)
+    A = _as_f64(A)
+    A = A.toarray() if hasattr(A, "toarray") else A
     if not raw:
         A = A - A.mean(axis=0)[None, :]
     G = A.T @ A if A.shape[0] >= A.shape[1] else A @ A.T

@@ -30,7 +30,7 @@ constexpr int kNB = 32;
 __global__ void __launch_bounds__(kCholThreads)
 chol_inv_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
                 const float *__restrict__ Racc_in, float *__restrict__ Racc_out,
-                DevStatus *__restrict__ st) {
+                DevStatus *__restrict__ st, int *__restrict__ shifted_out, const int *__restrict__ skip_flag) {
     extern __shared__ float sm[];
     const int ld = l + 1;
     float *R = sm;                        // l x ld
@@ -43,6 +43,14 @@ chol_inv_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
 
+    if (skip_flag && *skip_flag == 0) {                 // R = I
+        for (int e = tid; e < lp * lp; e += nt) Rinv[e] = ((e / lp) == (e % lp) && (e / lp) < l) ? 1.f : 0.f;
+        if (Racc_out)
+            for (int e = tid; e < l * l; e += nt)
+                Racc_out[e] = Racc_in ? Racc_in[e] : ((e / l == e % l) ? 1.f : 0.f);
+        if (shifted_out && tid == 0) *shifted_out = 0;
+        return;
+    }
     if (tid == 0) { s_bad = 0; s_maxdiag = 0.f; }
     __syncthreads();
     for (int e = tid; e < l * l; e += nt)
@@ -88,6 +96,7 @@ chol_inv_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__
         shift = (shift == 0.f) ? 16.f * (float)l * eps * fmaxf(maxdiag, 1e-30f) : shift * 100.f;
         if (tid == 0) atomicAdd(&st->shifts, 1);
     }
+    if (shifted_out && tid == 0) *shifted_out = (shift != 0.f || !ok) ? 1 : 0;
 
     if (!ok) {
         if (tid == 0) dev_fail(st, bad ? RPCA_ERR_NONFINITE : RPCA_ERR_BREAKDOWN);
@@ -175,13 +184,13 @@ chol_inv_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__
 }  // namespace
 
 int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
-                    float *Racc_out, DevStatus *st, cudaStream_t s) {
+                    float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out, const int *skip_flag) {
     const size_t smem = ((size_t)l * (l + 1) + (size_t)kNB * (l > kNB ? l - kNB : 1)) * sizeof(float);
     if (cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) + (size_t)kNB * (RPCA_MAX_L - kNB)) *
                                    sizeof(float))) != cudaSuccess)
         return RPCA_ERR_CUDA;
-    chol_inv_kernel<<<1, kCholThreads, smem, s>>>(G, l, lp, Rinv, Racc_in, Racc_out, st);
+    chol_inv_kernel<<<1, kCholThreads, smem, s>>>(G, l, lp, Rinv, Racc_in, Racc_out, st, shifted_out, skip_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

@@ -31,7 +31,7 @@ template <int BM, int BN, int TM, int TN, bool TRANS_A>
 __global__ void __launch_bounds__(kThreads)
 sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64_t lda,
              const float *__restrict__ B, int64_t ldb, float *__restrict__ C, int64_t ldc,
-             int64_t kchunk, int64_t split_stride) {
+             int64_t kchunk, int64_t split_stride, const int *__restrict__ copy_flag) {
     constexpr int BK = kBK;
     constexpr int TX = BN / TN;
     constexpr int TY = BM / TM;
@@ -49,6 +49,15 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64
     const int tx = tid % TX, ty = tid / TX;
     const int64_t m0 = (int64_t)blockIdx.x * BM;
     const int64_t n0 = (int64_t)blockIdx.y * BN;
+    if (!TRANS_A && copy_flag && *copy_flag == 0) {
+        // multiplication by the identity: C = A on this tile
+        if (blockIdx.z == 0)
+            for (int e = tid; e < BM * BN; e += kThreads) {
+                const int64_t r = m0 + e / BN, c = n0 + e % BN;
+                if (r < M && c < N) C[r * ldc + c] = A[r * lda + c];
+            }
+        return;
+    }
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = min(K, kbeg + kchunk);
     C += (int64_t)blockIdx.z * split_stride;
@@ -204,7 +213,7 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64
 template <int BM, int BN, int TM, int TN>
 int launch_cfg(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-               int64_t split_stride, cudaStream_t s) {
+               int64_t split_stride, cudaStream_t s, const int *copy_flag) {
     const int64_t kchunk = round_up(cdiv(K, splits), kBK);
     const int64_t gz = cdiv(K, kchunk);
     // slices past the end of K still write zero partials so the reduction sees `splits` slices
@@ -213,10 +222,10 @@ int launch_cfg(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, in
     if (grid.x > 2147483647u || grid.y > 65535u || grid.z > 65535u) return RPCA_ERR_INVALID_ARG;
     if (trans_a)
         sgemm_kernel<BM, BN, TM, TN, true><<<grid, kThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                                     kchunk, split_stride);
+                                                                     kchunk, split_stride, nullptr);
     else
         sgemm_kernel<BM, BN, TM, TN, false><<<grid, kThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                                      kchunk, split_stride);
+                                                                      kchunk, split_stride, copy_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
@@ -234,13 +243,13 @@ int choose_splits(int64_t M, int64_t N, int64_t K) {
 
 int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                  const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-                 int64_t split_stride, cudaStream_t s) {
+                 int64_t split_stride, cudaStream_t s, const int *copy_flag) {
     if (M <= 0 || N <= 0) return RPCA_OK;
     if (splits < 1) splits = 1;
-    if (N <= 16) return launch_cfg<128, 16, 4, 2>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s);
-    if (N <= 32) return launch_cfg<128, 32, 4, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s);
-    if (N <= 64) return launch_cfg<128, 64, 8, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s);
-    return launch_cfg<128, 128, 8, 8>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s);
+    if (N <= 16) return launch_cfg<128, 16, 4, 2>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
+    if (N <= 32) return launch_cfg<128, 32, 4, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
+    if (N <= 64) return launch_cfg<128, 64, 8, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
+    return launch_cfg<128, 128, 8, 8>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
 }
 
 }  // namespace rpca

@@ -69,9 +69,17 @@ int launch_omega(int64_t n, int l, uint64_t seed, uint64_t stream_id, const floa
 // C[M x N] (ldc) = op(A) B over the K range split into `splits` slices;
 // slice z writes C + z * split_stride.  op(A) = A (A is M x K, lda) when
 // !trans_a, and A^T (A stored K x M, lda) when trans_a.  B is K x N (ldb).
+// When copy_flag is given and *copy_flag == 0 (read on the device), the
+// kernel copies C = A (non-transposed, M x N) instead of multiplying.
 int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                  const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-                 int64_t split_stride, cudaStream_t s);
+                 int64_t split_stride, cudaStream_t s, const int *copy_flag = nullptr);
+
+// Partial Grams part[s] (lp x lp) = Y[chunk s]^T Y[chunk s] of a row-major Y
+// (rows x lp, ld = lp); skipped entirely when *skip_flag == 0.
+int launch_gram(const float *Y, int64_t rows, int lp, float *part, int splits, const int *skip_flag,
+                cudaStream_t s);
+int gram_splits(int64_t rows, int lp);
 
 // Number of K slices launch_sgemm should use so that the grid fills the GPU.
 int choose_splits(int64_t M, int64_t N, int64_t K);
@@ -92,7 +100,8 @@ int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value,
                     cudaStream_t s);
 
 // G (FP64, l x l) = sum over splits of the FP32 partial Grams part[s] (lp x lp).
-int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s);
+int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s,
+                       const int *skip_flag = nullptr);
 
 // X = sum_s part[s] (rows x lp); when centring, X[:, c] -= (X[:, l] / m) * qsum[c]
 // with qsum from the column-sum partials of Q; padding columns zeroed.
@@ -101,8 +110,12 @@ int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, in
 
 // One CTA: Cholesky G = R^T R in FP32 (shifted on breakdown), Rinv (lp x lp,
 // zero padded) = R^-1; optionally Racc_out = R * Racc_in (l x l, upper).
+// shifted_out (optional) receives 1 when the diagonal had to be shifted.
+// When skip_flag is given and *skip_flag == 0, R = I: Rinv = I and
+// Racc_out = Racc_in.
 int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
-                    float *Racc_out, DevStatus *st, cudaStream_t s);
+                    float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out = nullptr,
+                    const int *skip_flag = nullptr);
 
 // Small SVD of R^T (R = Racc, l x l upper): writes Wk (lp x kp, U-side
 // factors, k leading left singular vectors of R^T), sig (l, descending) and

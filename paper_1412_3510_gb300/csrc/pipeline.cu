@@ -6,7 +6,11 @@
 //   Q = renorm(Y)                       Section 5: renormalise every product
 //   its times: X = A_c^* Q; Q' = renorm(X); Y = A_c Q'; Q = renorm(Y)
 //   the last renormalisation is a full orthonormalisation (Section 5's QR),
-//   here CholeskyQR applied three times (the first shifted if needed)
+//   here CholeskyQR applied two times, three when the first had to shift
+//
+// A renormalisation Q = Y R^-1 on the m side that only feeds the next
+// adjoint product is never formed: A_c^* (Y R^-1) = (A_c^* Y) R^-1, so R^-1
+// is applied to the small n x l result instead.
 //   B^* = A_c^* Q; B^* = Q2 R (CholeskyQR x3); R^T = W Sigma Z^T (Jacobi)
 //   V = Q2 Z, U = Q W (Eq. i4), first k columns, sign convention on V.
 //
@@ -44,8 +48,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.lp = padded_l(l);
     L.kp = (int)round_up(k, 4);
     L.s_adj = adjoint_splits;
-    L.s_gram_m = choose_splits(L.lp, L.lp, m);
-    L.s_gram_n = choose_splits(L.lp, L.lp, n);
+    L.s_gram_m = gram_splits(m, L.lp);
+    L.s_gram_n = gram_splits(n, L.lp);
     L.cchunks = colsum_chunks(m);
     const size_t lp = (size_t)L.lp;
     size_t off = 0;
@@ -70,6 +74,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.perm = take(lp * 4);
     L.rot = take(small_svd_rot_floats(l) * 4);
     L.zbuf = take(256);
+    L.rinv_m = take(lp * lp * 4);
+    L.flags = take(256);
     L.scratch = take(op_scratch);
     L.total = off;
     return L;
@@ -99,78 +105,105 @@ struct Ctx {
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
 };
 
-// One CholeskyQR round: out = in R^-1 with G = in^T in = R^T R.
-int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int splits,
-                 const float *racc_in, float *racc_out) {
+// Gram, reduction and Cholesky of a tall block: rinv = R^-1 with in^T in = R^T R.
+int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *rinv, const float *racc_in,
+              float *racc_out, int *shifted_out, const int *skip) {
     const Layout &L = c.L;
     const int lp = L.lp;
     float *part = c.at<float>(L.part);
     double *G = c.at<double>(L.G);
-    float *rinv = c.at<float>(L.rinv);
     {
         TimedScope ts(kTimeGram, c.s);
-        RPCA_TRY(launch_sgemm(true, lp, lp, rows, in, lp, in, lp, part, lp, splits, (int64_t)lp * lp, c.s));
-        RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s));
+        RPCA_TRY(launch_gram(in, rows, lp, part, splits, skip, c.s));
+        RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s, skip));
     }
-    {
-        TimedScope ts(kTimeChol, c.s);
-        RPCA_TRY(launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s));
-    }
+    TimedScope ts(kTimeChol, c.s);
+    return launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s, shifted_out, skip);
+}
+
+// One CholeskyQR round: out = in R^-1.  With skip (*skip == 0 on the device) the round is
+// the identity and out = in.
+int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int splits, const float *racc_in,
+                 float *racc_out, int *shifted_out = nullptr, const int *skip = nullptr) {
+    const Layout &L = c.L;
+    const int lp = L.lp;
+    float *rinv = c.at<float>(L.rinv);
+    RPCA_TRY(gram_chol(c, in, rows, splits, rinv, racc_in, racc_out, shifted_out, skip));
     TimedScope ts(kTimeTrsm, c.s);
-    RPCA_TRY(launch_sgemm(false, rows, lp, lp, in, lp, rinv, lp, out, lp, 1, 0, c.s));
+    RPCA_TRY(launch_sgemm(false, rows, lp, lp, in, lp, rinv, lp, out, lp, 1, 0, c.s, skip));
     return RPCA_OK;
 }
 
-// m-side renormalisation of y0 (a fresh product A X) into y1.
-int renorm_m(const Ctx &c, bool raw, bool final_) {
+// m-side renormalisation of y0 (a fresh product A X).  Non-final: y0 is centred
+// and kept, R^-1 goes to rinv_m for the next adjoint product (implicit Q).
+// Final: explicit orthonormal Q in y1 (CholeskyQR two or three times).
+// Returns through *q the block the next adjoint product reads.
+int renorm_m(const Ctx &c, bool raw, bool final_, const float **q, bool *pending) {
     const Layout &L = c.L;
     float *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
+    int *flag = c.at<int>(L.flags);
     if (!raw) {
         TimedScope ts(kTimeCentre, c.s);
         int nch = 0;
         RPCA_TRY(launch_colsum_partial(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), &nch, c.s));
         RPCA_TRY(launch_center(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), nch, c.s));
     }
-    RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr));
-    if (final_) {
+    float *qout = y1;
+    if (!final_) {
+        RPCA_TRY(gram_chol(c, y0, L.m, L.s_gram_m, c.at<float>(L.rinv_m), nullptr, nullptr, nullptr, nullptr));
+        qout = y0;
+        *pending = true;
+    } else {
+        RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr, flag));
         RPCA_TRY(cholqr_round(c, y1, y0, L.m, L.s_gram_m, nullptr, nullptr));
-        RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr));
+        RPCA_TRY(cholqr_round(c, y0, y1, L.m, L.s_gram_m, nullptr, nullptr, nullptr, flag));
+        *pending = false;
     }
-    RPCA_TRY(launch_finalize(y1, L.m, L.l, L.lp, raw ? 0.f : 1.f, raw ? nullptr : c.at<float>(L.qpart), c.s));
+    RPCA_TRY(launch_finalize(qout, L.m, L.l, L.lp, raw ? 0.f : 1.f, raw ? nullptr : c.at<float>(L.qpart), c.s));
+    *q = qout;
     return RPCA_OK;
 }
 
 // n-side renormalisation of x0 (a fresh product A^T Q) into x1; the final one
-// accumulates the triangular factor R = R3 R2 R1 into racc0.
+// accumulates the triangular factor R = R3 R2 R1 into racc0 (R3 = I when the
+// first round did not shift).
 int renorm_n(const Ctx &c, bool final_) {
     const Layout &L = c.L;
     float *x0 = c.at<float>(L.x0), *x1 = c.at<float>(L.x1);
     float *r0 = c.at<float>(L.racc0), *r1 = c.at<float>(L.racc1);
+    int *flag = c.at<int>(L.flags) + 1;
     if (!final_) return cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, nullptr);
-    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, r0));
+    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, r0, flag));
     RPCA_TRY(cholqr_round(c, x1, x0, L.n, L.s_gram_n, r0, r1));
-    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, r1, r0));
+    RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, r1, r0, nullptr, flag));
     return RPCA_OK;
 }
 
-// x0 = A_c^* y1  (Section 5: (Q'*A)' - c'*(ones(1,m)*Q)).
-int adjoint_pass(const Operator &op, const Ctx &c, bool raw) {
+// x0 = A_c^* q  (Section 5: (Q'*A)' - c'*(ones(1,m)*Q)), times the pending R^-1 of an
+// implicit m-side renormalisation.
+int adjoint_pass(const Operator &op, const Ctx &c, bool raw, const float *q, bool pending) {
     const Layout &L = c.L;
     float *part = c.at<float>(L.part);
     {
         TimedScope ts(kTimeAdjoint, c.s);
-        RPCA_TRY(op.adjoint(c.at<float>(L.y1), L.lp, part, c.s));
+        RPCA_TRY(op.adjoint(q, L.lp, part, c.s));
     }
     const int splits = op.adjoint_splits(L.lp);
-    RPCA_TRY(launch_adjoint_reduce(part, std::max(splits, 1), L.n, L.l, L.lp, c.at<float>(L.x0), raw ? 0 : 1,
-                                   (double)L.m, c.at<float>(L.qpart), L.cchunks, c.s));
+    float *dst = pending ? c.at<float>(L.x1) : c.at<float>(L.x0);
+    RPCA_TRY(launch_adjoint_reduce(part, std::max(splits, 1), L.n, L.l, L.lp, dst, raw ? 0 : 1, (double)L.m,
+                                   c.at<float>(L.qpart), L.cchunks, c.s));
+    if (pending) {
+        TimedScope ts(kTimeTrsm, c.s);
+        RPCA_TRY(launch_sgemm(false, L.n, L.lp, L.lp, dst, L.lp, c.at<float>(L.rinv_m), L.lp, c.at<float>(L.x0), L.lp,
+                              1, 0, c.s));
+    }
     return RPCA_OK;
 }
 
 }  // namespace
 
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
-                 int64_t ldv, void *ws, const Layout &L, cudaStream_t s) {
+                 int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status) {
     Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status)};
     op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
     op.st = c.st;
@@ -178,7 +211,7 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     const int l = L.l, lp = L.lp;
     float *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
 
-    if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (clear_status && cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
     if (cudaMemsetAsync(x1, 0, (size_t)L.n * lp * 4, s) != cudaSuccess) return RPCA_ERR_CUDA;
 
     // test matrix (Section 2), optionally weighted by d (Omega' = diag(d) Omega)
@@ -195,17 +228,19 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
         return op.apply(x1, lp, y0, s);
     };
     // sketch and power iterations
+    const float *q = nullptr;
+    bool pending = false;
     RPCA_TRY(apply());
-    RPCA_TRY(renorm_m(c, raw, o->its == 0));
+    RPCA_TRY(renorm_m(c, raw, o->its == 0, &q, &pending));
     for (int it = 1; it <= o->its; ++it) {
-        RPCA_TRY(adjoint_pass(op, c, raw));
+        RPCA_TRY(adjoint_pass(op, c, raw, q, pending));
         RPCA_TRY(renorm_n(c, false));
         RPCA_TRY(apply());
-        RPCA_TRY(renorm_m(c, raw, it == o->its));
+        RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending));
     }
 
     // B^* = A_c^* Q (Eq. i2), B^* = Q2 R, SVD of R^T (Eq. i3)
-    RPCA_TRY(adjoint_pass(op, c, raw));
+    RPCA_TRY(adjoint_pass(op, c, raw, q, pending));
     RPCA_TRY(renorm_n(c, true));
     float *wk = c.at<float>(L.wk), *zk = c.at<float>(L.zk), *sig = c.at<float>(L.sig);
     {

@@ -84,7 +84,9 @@ center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
 // result carries FP32-level relative error, as the FP32 Cholesky needs; GB300's
 // FP64 adds run at 1/64 of the FP32 rate.
 __global__ void __launch_bounds__(256)
-gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G) {
+gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G,
+                   const int *__restrict__ skip_flag) {
+    if (skip_flag && *skip_flag == 0) return;
     const int64_t total = (int64_t)l * l;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -184,9 +186,10 @@ int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, 
     return RPCA_OK;
 }
 
-int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s) {
+int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s,
+                       const int *skip_flag) {
     const int64_t grid = std::min<int64_t>(cdiv((int64_t)l * l, 256), (int64_t)num_sms() * 2);
-    gram_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(part, splits, l, lp, G);
+    gram_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(part, splits, l, lp, G, skip_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

@@ -184,7 +184,7 @@ ResidLayout make_resid_layout(int64_t m, int64_t n, int k, int adj_splits) {
 
 int run_resid(const Operator &op, int raw, const float *U, int64_t ldu, const float *S, const float *V,
               int64_t ldv, int k, int iters, uint64_t seed, double *est, void *ws, const ResidLayout &R,
-              cudaStream_t s) {
+              cudaStream_t s, bool clear_status) {
     char *w = reinterpret_cast<char *>(ws);
     auto F = [&](size_t o) { return reinterpret_cast<float *>(w + o); };
     DevStatus *st = reinterpret_cast<DevStatus *>(w + R.status);
@@ -194,7 +194,7 @@ int run_resid(const Operator &op, int raw, const float *U, int64_t ldu, const fl
     const int64_t m = R.m, n = R.n;
     const int centre = raw ? 0 : 1;
 
-    if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (clear_status && cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
     if (cudaMemsetAsync(x8, 0, (size_t)n * kW * 4, s) != cudaSuccess) return RPCA_ERR_CUDA;
     if (cudaMemsetAsync(est, 0, sizeof(double), s) != cudaSuccess) return RPCA_ERR_CUDA;
     RPCA_TRY(launch_omega(n, 1, seed, 1, nullptr, x8, kW, s));

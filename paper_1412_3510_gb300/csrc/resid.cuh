@@ -16,6 +16,6 @@ ResidLayout make_resid_layout(int64_t m, int64_t n, int k, int adj_splits);
 
 int run_resid(const Operator &op, int raw, const float *U, int64_t ldu, const float *S, const float *V,
               int64_t ldv, int k, int iters, uint64_t seed, double *est, void *ws, const ResidLayout &R,
-              cudaStream_t s);
+              cudaStream_t s, bool clear_status = true);
 
 }  // namespace rpca

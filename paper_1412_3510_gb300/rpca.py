@@ -223,3 +223,72 @@ def rpca_dense_pass(A: torch.Tensor, B: torch.Tensor, adjoint: bool = False, pre
     if check:
         _check(rpca_read_status(ws, stream), "rpca_dense_pass (device)")
     return C
+
+
+def _need_i32(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32:
+        raise ValueError(f"{name} must be an int32 CUDA tensor")
+
+
+def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, shape, k: int,
+             l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
+             omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
+             ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+    """Randomized PCA of a CSR matrix (row_ptr int32 m+1, col_idx int32 nnz, val float32 nnz)."""
+    m, n = int(shape[0]), int(shape[1])
+    _need_i32(row_ptr, "row_ptr")
+    _need_i32(col_idx, "col_idx")
+    _need_cuda(val, "val")
+    nnz = int(val.numel())
+    if omega is not None:
+        _need_cuda(omega, "omega")
+        omega = omega.contiguous()
+    if col_weights is not None:
+        _need_cuda(col_weights, "col_weights")
+        col_weights = col_weights.contiguous()
+    opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr", omega, col_weights)
+    lib = L.load()
+    need = int(lib.rpca_csr_workspace_size(m, n, nnz, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_csr_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, val.device)
+    if out is None:
+        U = torch.empty(m, k, dtype=torch.float32, device=val.device)
+        S = torch.empty(k, dtype=torch.float32, device=val.device)
+        V = torch.empty(n, k, dtype=torch.float32, device=val.device)
+    else:
+        U, S, V = out
+    code = lib.rpca_csr(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), C.byref(opts), _ptr(U),
+                        _rowmajor_ld(U, "U"), _ptr(S), _ptr(V), _rowmajor_ld(V, "V"), _ptr(ws), ws.numel(),
+                        _stream(stream))
+    _check(code, "rpca_csr")
+    if check:
+        _check(rpca_read_status(ws, stream), "rpca_csr (device)")
+    return U, S, V
+
+
+def rpca_resid_norm_csr(row_ptr, col_idx, val, shape, U, S, V, raw: bool = False, iters: int = 20,
+                        seed: int = 0, ws=None, est=None, stream=None, sync: bool = True):
+    """Section 4 residual estimate for a CSR matrix."""
+    m, n = int(shape[0]), int(shape[1])
+    nnz = int(val.numel())
+    k = int(S.numel())
+    lib = L.load()
+    need = int(lib.rpca_resid_csr_workspace_size(m, n, nnz, k))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_resid_csr_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, val.device)
+    if est is None:
+        est = torch.empty(1, dtype=torch.float64, device=val.device)
+    ldu = _rowmajor_ld(U, "U") if k else k
+    ldv = _rowmajor_ld(V, "V") if k else k
+    code = lib.rpca_resid_norm_csr(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), int(bool(raw)), _ptr(U),
+                                   ldu, _ptr(S), _ptr(V), ldv, k, int(iters), seed & ((1 << 64) - 1), _ptr(est),
+                                   _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "rpca_resid_norm_csr")
+    if sync:
+        _check(rpca_read_status(ws, stream), "rpca_resid_norm_csr (device)")
+        return float(est.item())
+    return est

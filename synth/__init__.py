@@ -266,4 +266,10 @@ WORKLOADS = {
     # than L2) for profiler captures that must stay small
     "dense_25000x2000_k100": dict(m=25000, n=2000, k=100, l=102, its=2, raw=False,
                                   spectrum=lambda r: spectrum_pow15(r, 1236), seed=1238),
+    # sparse: power-law row/column degrees (exponent 2.1), N(0,1) values plus a planted
+    # rank-30 part on the pattern
+    "csr_1000000x100000_k30": dict(kind="csr", m=1000000, n=100000, nnz=10000000, exponent=2.1, rank=30,
+                                   k=30, l=32, its=4, raw=True, seed=1239),
+    "csr_100000x10000_k30": dict(kind="csr", m=100000, n=10000, nnz=1000000, exponent=2.1, rank=30,
+                                 k=30, l=32, its=4, raw=True, seed=1240),
 }

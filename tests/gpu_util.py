@@ -25,3 +25,18 @@ def subspace_dist(X, Y):
     Qy, _ = np.linalg.qr(Y)
     return np.linalg.norm(Qx @ Qx.T - Qy @ Qy.T, 2) if Qx.shape[0] <= 3000 else \
         np.sqrt(max(0.0, 1.0 - np.linalg.svd(Qx.T @ Qy, compute_uv=False).min() ** 2))
+
+
+def subspace_tol(s_ref, k, rel_pert=3e-5):
+    """(kk, tol): the leading kk singular vectors to compare and the bound on their
+    subspace distance.  Wedin's theorem: a perturbation of relative size rel_pert
+    (FP32 or split-BF16 arithmetic) moves the leading-kk singular subspace by at most
+    about rel_pert * s_1 / (s_kk - s_{kk+1}); the bound never goes below 1e-3.
+    kk < k so that s_{kk+1} is known; values below 1e-3 s_1 are left out."""
+    import numpy as np
+    s_ref = np.asarray(s_ref)
+    kk = min(k - 1, int(np.sum(s_ref > 1e-3 * s_ref[0])))
+    if kk < 1:
+        return 0, 0.0
+    gap = max(s_ref[kk - 1] - s_ref[kk], 1e-300)
+    return kk, max(1e-3, rel_pert * s_ref[0] / gap)
