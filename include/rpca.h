@@ -123,6 +123,39 @@ int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const in
              float *V, int64_t ldv, void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Batched randomized PCA of many small dense matrices in one launch (the same
+ * method as rpca_dense, Sections 2 and 5; one persistent kernel, each CTA
+ * carrying whole PCAs, largest matrices first).
+ *
+ * descs       : count descriptors (device memory), one per matrix; U, S, V
+ *               are that matrix's outputs (device), as for rpca_dense.
+ * max_m       : an upper bound on every descriptor's m (sizes the workspace).
+ * max_n       : an upper bound on every descriptor's n.
+ * o           : k <= l <= 32 and l <= min(m, n) for every matrix;
+ *               n * round_up(l + 1, 8) <= 24576; o->omega must be NULL; o->seed
+ *               keys Omega exactly as in rpca_dense; precision is FP32.
+ * col_weights : NULL, or a device array of count device pointers, each NULL
+ *               or an n-vector d: that matrix's sketch uses diag(d) Omega.
+ * item_status : NULL, or count int32 (device): 0 on success, RPCA_ERR_INVALID_ARG
+ *               for a descriptor that breaks the rules above (that matrix is
+ *               skipped; the others are computed).
+ * ---------------------------------------------------------------------- */
+typedef struct rpca_mat_desc {
+    const float *A;
+    int64_t m, n, lda;
+    float *U;
+    int64_t ldu;
+    float *S;
+    float *V;
+    int64_t ldv;
+} rpca_mat_desc;
+
+size_t rpca_batched_workspace_size(int32_t count, int64_t max_m, int64_t max_n, const rpca_opts *o);
+int rpca_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n, const rpca_opts *o,
+                 const float *const *col_weights, int32_t *item_status, void *ws, size_t ws_bytes,
+                 rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Spectral-norm residual estimate ||A_c - U diag(S) V^T||_2 by the power
  * method from a random start (Section 4).
  *

@@ -5,7 +5,7 @@ include/rpca.h); ``rpca`` holds the Python binding with the same entry-point
 names.  ``build.build()`` compiles the library in-tree.
 """
 from .rpca import (RpcaError, rpca_dense, rpca_dense_workspace_size, rpca_gaussian_omega,  # noqa: F401
-                   rpca_resid_norm, rpca_dense_pass, rpca_csr, rpca_resid_norm_csr,
+                   rpca_resid_norm, rpca_dense_pass, rpca_csr, rpca_resid_norm_csr, Batch, rpca_batched,
                    rpca_launch_count, rpca_philox4x64_10, rpca_read_status, make_opts,
                    read_status_block, workspace, rpca_timing_enable, rpca_timing_reset,
                    rpca_timing_read)

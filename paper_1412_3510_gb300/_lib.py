@@ -49,6 +49,8 @@ SIGNATURES = [
     ("rpca_resid_csr_workspace_size", _SZ, [_I64, _I64, _I64, _I32]),
     ("rpca_resid_norm_csr", C.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, _P, _I64, _P, _P, _I64, _I32, _I32, _U64,
                                       _P, _P, _SZ, _P]),
+    ("rpca_batched_workspace_size", _SZ, [_I32, _I64, _I64, _OPTS]),
+    ("rpca_batched", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),

@@ -48,8 +48,8 @@ int check_launch();   // RPCA_OK or RPCA_ERR_CUDA after a <<<>>> launch
         if (_e < 0) return _e;                               \
     } while (0)
 
-static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
-static inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 // Padded sketch width: at least one spare column (the ones column that
 // carries the column sums of A through the adjoint products), multiple of 8.

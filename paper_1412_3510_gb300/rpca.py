@@ -292,3 +292,53 @@ def rpca_resid_norm_csr(row_ptr, col_idx, val, shape, U, S, V, raw: bool = False
         _check(rpca_read_status(ws, stream), "rpca_resid_norm_csr (device)")
         return float(est.item())
     return est
+
+
+class Batch:
+    """Device-side descriptors for rpca_batched: one (A, U, S, V) per matrix.
+
+    mats: list of m_i x n_i float32 CUDA tensors (row-major).  Outputs are
+    allocated here (U_i m_i x k, S_i k, V_i n_i x k)."""
+
+    def __init__(self, mats, k: int, device=None):
+        device = device or mats[0].device
+        self.mats = mats
+        self.k = k
+        self.U = [torch.empty(a.shape[0], k, dtype=torch.float32, device=device) for a in mats]
+        self.S = [torch.empty(k, dtype=torch.float32, device=device) for _ in mats]
+        self.V = [torch.empty(a.shape[1], k, dtype=torch.float32, device=device) for a in mats]
+        rows = []
+        for a, u, s_, v in zip(mats, self.U, self.S, self.V):
+            _need_cuda(a, "A")
+            rows.append([a.data_ptr(), a.shape[0], a.shape[1], _rowmajor_ld(a, "A"), u.data_ptr(), k,
+                         s_.data_ptr(), v.data_ptr(), k])
+        self.desc = torch.tensor(rows, dtype=torch.int64, device=device)   # 9 x 8-byte fields per matrix
+        self.max_m = max(a.shape[0] for a in mats)
+        self.max_n = max(a.shape[1] for a in mats)
+        self.status = torch.zeros(len(mats), dtype=torch.int32, device=device)
+
+
+def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
+                 col_weights=None, ws: torch.Tensor | None = None, stream=None, check: bool = True):
+    """Randomized PCA of every matrix of `batch` in one launch.  col_weights: None or a
+    list of per-matrix n-vectors (or None entries).  Returns (U list, S list, V list)."""
+    k = batch.k
+    opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr")
+    lib = L.load()
+    count = len(batch.mats)
+    need = int(lib.rpca_batched_workspace_size(count, batch.max_m, batch.max_n, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_batched_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, batch.desc.device)
+    wptr = None
+    if col_weights is not None:
+        wptr = torch.tensor([0 if w is None else w.data_ptr() for w in col_weights], dtype=torch.int64,
+                            device=batch.desc.device)
+        batch._wkeep = (col_weights, wptr)
+    code = lib.rpca_batched(count, _ptr(batch.desc), batch.max_m, batch.max_n, C.byref(opts), _ptr(wptr),
+                            _ptr(batch.status), _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "rpca_batched")
+    if check:
+        _check(rpca_read_status(ws, stream), "rpca_batched (device)")
+    return batch.U, batch.S, batch.V
