@@ -28,9 +28,9 @@ constexpr int kBN = 128;                   // columns per A tile (A^T Y)
 constexpr int kJacSweeps = 30;
 constexpr int kGramGroups = 16;            // row groups of the Gram
 constexpr int kMaxPairs = 64;              // 4x4 blocks of the upper triangle, lp <= 40 -> 55
-constexpr int kTileFloats = kGramGroups * kMaxPairs * 16 > kBK * (kBN + 4) + kBK * kMaxLP
+constexpr int kTileFloats = kGramGroups * kMaxPairs * 16 > kBK * (256 + 4) + kBK * kMaxLP
                                 ? kGramGroups * kMaxPairs * 16
-                                : kBK * (kBN + 4) + kBK * kMaxLP;
+                                : kBK * (256 + 4) + kBK * kMaxLP;
 
 struct Item {
     const float *A;
@@ -100,30 +100,50 @@ __device__ void gen_omega(Smem &sm, int64_t n, int l, int lp, uint64_t seed, con
     __syncthreads();
 }
 
-// Y (m x lp, global) = A X (X = sm.X, n x lp).  Thread: 2 rows x CPT columns.
+// Y (m x lp, global) = A X (X = sm.X, n x lp).  Thread: 4 rows x CPT columns; the next A
+// tile is fetched into registers while the current one is multiplied.
 template <int CPT>
 __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int lp,
                          float *__restrict__ Y) {
-    float *As = sm.tile;                          // [kBK][kBM + 4]
+    constexpr int BM = 256, LDT = BM + 4;
+    float *As = sm.tile;                          // [kBK][LDT]
     const int tid = threadIdx.x;
-    const int rp = tid >> 3, cg = tid & 7;        // 64 row pairs x 8 column groups
-    for (int64_t r0 = 0; r0 < m; r0 += kBM) {
-        float acc[2][CPT];
+    const int rq = tid >> 3, cg = tid & 7;        // 64 row quads x 8 column groups
+    constexpr int PER = BM * kBK / kThreads;      // 16 elements of a tile per thread
+    float pre[PER];
+    auto fetch = [&](int64_t r0, int64_t k0) {
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            const int r = e / kBK, kk = e % kBK;
+            const int64_t gr = r0 + r, gk = k0 + kk;
+            pre[q] = (gr < m && gk < n) ? __ldg(A + gr * lda + gk) : 0.f;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            As[(e % kBK) * LDT + e / kBK] = pre[q];
+        }
+    };
+    const int64_t ktiles = (n + kBK - 1) / kBK;
+    for (int64_t r0 = 0; r0 < m; r0 += BM) {
+        float acc[4][CPT];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int q = 0; q < CPT; ++q) acc[a][q] = 0.f;
-        for (int64_t k0 = 0; k0 < n; k0 += kBK) {
+        fetch(r0, 0);
+        for (int64_t t = 0; t < ktiles; ++t) {
+            const int64_t k0 = t * kBK;
             __syncthreads();
-            for (int e = tid; e < kBM * kBK; e += blockDim.x) {
-                const int r = e / kBK, kk = e % kBK;
-                const int64_t gr = r0 + r, gk = k0 + kk;
-                As[kk * (kBM + 4) + r] = (gr < m && gk < n) ? __ldg(A + gr * lda + gk) : 0.f;
-            }
+            stash();
             __syncthreads();
+            if (t + 1 < ktiles) fetch(r0, k0 + kBK);
             const int kn = (int)min((int64_t)kBK, n - k0);
             for (int kk = 0; kk < kn; ++kk) {
-                const float2 a = *reinterpret_cast<const float2 *>(&As[kk * (kBM + 4) + 2 * rp]);
+                const float4 a = *reinterpret_cast<const float4 *>(&As[kk * LDT + 4 * rq]);
                 const float *xr = sm.X + (k0 + kk) * lp;
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
@@ -131,12 +151,14 @@ __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64
                     const float x = c < lp ? xr[c] : 0.f;
                     acc[0][q] = fmaf(a.x, x, acc[0][q]);
                     acc[1][q] = fmaf(a.y, x, acc[1][q]);
+                    acc[2][q] = fmaf(a.z, x, acc[2][q]);
+                    acc[3][q] = fmaf(a.w, x, acc[3][q]);
                 }
             }
         }
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int64_t r = r0 + 2 * rp + a;
+        for (int a = 0; a < 4; ++a) {
+            const int64_t r = r0 + 4 * rq + a;
             if (r < m)
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
@@ -148,36 +170,67 @@ __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64
     __syncthreads();
 }
 
-// X (n x lp, shared) = A^T Y (Y global, m x lp).  Thread: 2 columns of A x CPT columns of Y.
+// X (n x lp, shared) = A^T Y (Y global, m x lp).  Thread: 4 columns of A x CPT columns of Y;
+// the next tiles are fetched into registers while the current ones are multiplied.
 template <int CPT>
 __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int lp,
                           const float *__restrict__ Y) {
-    float *As = sm.tile;                          // [kBK][kBN + 4]
-    float *Ys = sm.tile + kBK * (kBN + 4);        // [kBK][lp]
+    constexpr int BN = 256, LDT = BN + 4;
+    float *As = sm.tile;                          // [kBK][LDT]
+    float *Ys = sm.tile + kBK * LDT;              // [kBK][lp]
     const int tid = threadIdx.x;
-    const int cp = tid >> 3, cg = tid & 7;        // 64 column pairs x 8 column groups of Y
-    for (int64_t c0 = 0; c0 < n; c0 += kBN) {
-        float acc[2][CPT];
+    const int cq = tid >> 3, cg = tid & 7;        // 64 column quads x 8 column groups of Y
+    constexpr int PER = BN * kBK / kThreads;      // 16
+    float pre[PER], prey[(kBK * kMaxLP + kThreads - 1) / kThreads];
+    auto fetch = [&](int64_t c0, int64_t r0) {
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            const int rr = e / BN, cc = e % BN;
+            const int64_t gr = r0 + rr, gc = c0 + cc;
+            pre[q] = (gr < m && gc < n) ? __ldg(A + gr * lda + gc) : 0.f;
+        }
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) acc[a][q] = 0.f;
-        for (int64_t r0 = 0; r0 < m; r0 += kBK) {
-            __syncthreads();
-            for (int e = tid; e < kBK * kBN; e += blockDim.x) {
-                const int rr = e / kBN, cc = e % kBN;
-                const int64_t gr = r0 + rr, gc = c0 + cc;
-                As[rr * (kBN + 4) + cc] = (gr < m && gc < n) ? __ldg(A + gr * lda + gc) : 0.f;
-            }
-            for (int e = tid; e < kBK * lp; e += blockDim.x) {
+        for (int q = 0; q < (kBK * kMaxLP + kThreads - 1) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            float v = 0.f;
+            if (e < kBK * lp) {
                 const int rr = e / lp;
                 const int64_t gr = r0 + rr;
-                Ys[e] = gr < m ? Y[gr * lp + (e - rr * lp)] : 0.f;
+                if (gr < m) v = Y[gr * lp + (e - rr * lp)];
             }
+            prey[q] = v;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * kThreads;
+            As[(e / BN) * LDT + e % BN] = pre[q];
+        }
+#pragma unroll
+        for (int q = 0; q < (kBK * kMaxLP + kThreads - 1) / kThreads; ++q) {
+            const int e = tid + q * kThreads;
+            if (e < kBK * lp) Ys[e] = prey[q];
+        }
+    };
+    const int64_t rtiles = (m + kBK - 1) / kBK;
+    for (int64_t c0 = 0; c0 < n; c0 += BN) {
+        float acc[4][CPT];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) acc[a][q] = 0.f;
+        fetch(c0, 0);
+        for (int64_t t = 0; t < rtiles; ++t) {
+            const int64_t r0 = t * kBK;
             __syncthreads();
+            stash();
+            __syncthreads();
+            if (t + 1 < rtiles) fetch(c0, r0 + kBK);
             const int kn = (int)min((int64_t)kBK, m - r0);
             for (int kk = 0; kk < kn; ++kk) {
-                const float2 a = *reinterpret_cast<const float2 *>(&As[kk * (kBN + 4) + 2 * cp]);
+                const float4 a = *reinterpret_cast<const float4 *>(&As[kk * LDT + 4 * cq]);
                 const float *yr = Ys + kk * lp;
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
@@ -185,12 +238,14 @@ __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int6
                     const float y = c < lp ? yr[c] : 0.f;
                     acc[0][q] = fmaf(a.x, y, acc[0][q]);
                     acc[1][q] = fmaf(a.y, y, acc[1][q]);
+                    acc[2][q] = fmaf(a.z, y, acc[2][q]);
+                    acc[3][q] = fmaf(a.w, y, acc[3][q]);
                 }
             }
         }
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int64_t col = c0 + 2 * cp + a;
+        for (int a = 0; a < 4; ++a) {
+            const int64_t col = c0 + 4 * cq + a;
             if (col < n)
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {

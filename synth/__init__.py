@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "spectrum_exp20", "spectrum_pow15", "spectrum_exp50", "spectrum_section7",
     "haar_dense_np", "haar_dense_torch", "e2_matrix_np", "propack_diag",
-    "powerlaw_csr", "kernel_matrix_np", "kernel_batch_specs", "KernelSpec",
+    "powerlaw_csr", "kernel_matrix_np", "kernel_matrix_torch", "kernel_batch_specs", "KernelSpec",
     "WORKLOADS",
 ]
 
@@ -240,6 +240,19 @@ def kernel_batch_specs(count: int, seed: int, m_range=(256, 8192), n_range=(64, 
             for a, b, c, d in zip(lm, ln, lh, seeds)]
 
 
+def kernel_matrix_torch(spec: KernelSpec, device="cuda", noise_var: float = 1e-4):
+    """Same family on a torch device (torch's generator, seeded by spec.seed), FP32."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(spec.seed)
+    x = torch.rand(spec.m, 3, generator=g, device=device, dtype=torch.float32)
+    y = torch.rand(spec.n, 3, generator=g, device=device, dtype=torch.float32)
+    d2 = (x * x).sum(1)[:, None] + (y * y).sum(1)[None, :] - 2.0 * (x @ y.T)
+    a = torch.exp(-d2.clamp_min(0.0) / spec.h)
+    a += math.sqrt(noise_var) * torch.randn(spec.m, spec.n, generator=g, device=device, dtype=torch.float32)
+    return a
+
+
 def kernel_matrix_np(spec: KernelSpec, noise_var: float = 1e-4) -> np.ndarray:
     """A_ij = exp(-|x_i - y_j|^2 / h) + N(0, noise_var), x, y ~ U[0,1]^3, FP32."""
     rng = np.random.default_rng(spec.seed)
@@ -272,4 +285,10 @@ WORKLOADS = {
                                    k=30, l=32, its=4, raw=True, seed=1239),
     "csr_100000x10000_k30": dict(kind="csr", m=100000, n=10000, nnz=1000000, exponent=2.1, rank=30,
                                  k=30, l=32, its=4, raw=True, seed=1240),
+    # batched: Gaussian-kernel matrices exp(-|x_i - y_j|^2 / h) + N(0, 1e-4), m and n
+    # log-uniform, x, y ~ U[0,1]^3, h log-uniform in [0.05, 1]
+    "batched_4096_kernel_k16": dict(kind="batched", count=4096, m_range=(256, 8192), n_range=(64, 1024),
+                                    k=16, l=20, its=2, raw=False, seed=1241),
+    "batched_512_kernel_k16": dict(kind="batched", count=512, m_range=(256, 8192), n_range=(64, 1024),
+                                   k=16, l=20, its=2, raw=False, seed=1242),
 }
