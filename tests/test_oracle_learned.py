@@ -1,0 +1,79 @@
+"""Pins for the oracle's learned-weighting pieces: finite differences for the MLP
+gradient, closed forms for the features, the label on known singular vectors."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+
+L = O.learned_oracle
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    p = L.init_params(1)
+    F = rng.standard_normal((40, L.F_IN))
+    t = rng.standard_normal(40)
+    loss, g = L.loss_grad(p, F, t)
+    idx = np.concatenate([rng.choice(L.N_PARAMS, 60, replace=False), [L.N_PARAMS - 1]])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (L.loss_grad(p + e, F, t)[0] - L.loss_grad(p - e, F, t)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_forward_closed_form_linear_regime():
+    # with every pre-activation positive the MLP is the affine map w3^T (W2^T (W1^T f + b1) + b2) + b3
+    p = np.abs(L.init_params(2))
+    W1, b1, W2, b2, w3, b3 = L.split_params(p)
+    f = np.abs(np.random.default_rng(3).standard_normal((5, L.F_IN)))
+    y, _ = L.forward(p, f)
+    ref = ((f @ W1 + b1) @ W2 + b2) @ w3 + b3
+    assert np.allclose(y, ref, rtol=1e-12)
+
+
+def test_features_closed_forms():
+    A = S.kernel_matrix_np(S.KernelSpec(300, 80, 0.3, 5)).astype(np.float64)
+    F = L.features(A, raw=False, seed=4)
+    # relative energies average to ~0 in log; scaling one column by s shifts its f0 by 2 log s
+    B = A.copy()
+    B[:, 7] *= 3.0
+    G = L.features(B, raw=False, seed=4)
+    q = ((A - A.mean(0)) ** 2).sum(0)
+    qb = q.copy(); qb[7] *= 9.0
+    assert np.isclose(G[7, 0] - F[7, 0], math.log(9.0) - math.log(qb.mean() / q.mean()), atol=1e-9)
+    # f1 is the column mean over sqrt(qbar / m); f11, f12 the log sizes
+    assert np.allclose(F[:, 1], A.mean(0) / math.sqrt(q.mean() / 300), rtol=1e-9)
+    assert np.allclose(F[:, 11], math.log(300) / 8) and np.allclose(F[:, 12], math.log(80) / 8)
+    # sketch features have unit mean square per row, and are invariant to scaling A
+    assert np.allclose((F[:, 3:11] ** 2).mean(0), 1.0)
+    assert np.allclose(L.features(5.0 * A, seed=4)[:, 3:11], F[:, 3:11], rtol=1e-9, atol=1e-12)
+    assert np.all(F[:, 13:] == 0)
+
+
+def test_leverage_target_on_known_vectors():
+    n, k = 50, 4
+    V = np.zeros((n, k))
+    V[np.arange(k), np.arange(k)] = 1.0           # leverage 1 on 4 columns, 0 elsewhere
+    t = L.leverage_target(V, k)
+    assert np.allclose(t[:k], math.log(n / k + 1e-3)) and np.allclose(t[k:], math.log(1e-3))
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((n, k)))
+    assert np.isclose(np.exp(L.leverage_target(Q, k)).sum(), n + n * 1e-3)
+
+
+def test_adam_step_decreases_loss():
+    rng = np.random.default_rng(7)
+    p = L.init_params(3)
+    F = rng.standard_normal((200, L.F_IN))
+    t = F[:, 0] - 0.5 * F[:, 1]
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    l0 = L.loss_grad(p, F, t)[0]
+    for step in range(1, 201):
+        _, g = L.loss_grad(p, F, t)
+        p, m1, m2 = L.adam_step(p, g, m1, m2, step, 1e-3)
+    assert L.loss_grad(p, F, t)[0] < 0.2 * l0
