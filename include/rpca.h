@@ -219,6 +219,96 @@ int rpca_dense_pass_noalloc(const float *A, int64_t m, int64_t n, int64_t lda, i
                             int32_t w, float *C, int32_t precision, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Learned column weighting of the test matrix.
+ *
+ * Section 2 draws Omega with i.i.d. Gaussian entries; Section 5 notes that the
+ * method does not rely on the exact law of the test vectors.  The learned
+ * variant (not in the paper) uses diag(d) Omega, d_j > 0 predicted per column
+ * of A by an MLP 16 -> 128 -> 128 -> 1 (ReLU) from column statistics and a
+ * coarse 8-row Gaussian sketch, d_j = clip(exp(y_j), 1e-2, 1e2).  The MLP is
+ * trained (rpca_mlp_loss_grad, rpca_mlp_adam) to output the log relative
+ * leverage t_j = log(n |V_k[j, :]|^2 / k + 1e-3) (rpca_leverage_target).
+ *
+ * Parameters (FP32, RPCA_MLP_PARAMS values, device) in this order, row-major:
+ *   W1 [16][128], b1 [128], W2 [128][128], b2 [128], w3 [128], b3;
+ *   y = w3 . relu(W2^T relu(W1^T f + b1) + b2) + b3.
+ * Features (FP32, 16 per column, row-major n x 16), with c_j the column mean
+ * (0 when raw), q_j = |a_j - c_j|^2, qbar = mean q, tau = 1e-12 qbar + 1e-30,
+ * x_j = max |a_ij - c_j|, S = G^T (A - 1 c) for G m x 8 N(0,1) from the Philox
+ * stream (seed, 2) (the mapping of rpca_gaussian_omega), rho_r = rms_j S[r, j]:
+ *   log((q_j + tau) / (qbar + tau)), c_j / sqrt(qbar / m + tau),
+ *   log((x_j^2 m + tau) / (q_j + tau)) / 4, S[0..7, j] / (rho_r + 1e-30),
+ *   log(m) / 8, log(n) / 8, 0, 0, 0.
+ * ---------------------------------------------------------------------- */
+#define RPCA_MLP_FEATURES 16
+#define RPCA_MLP_HIDDEN 128
+#define RPCA_MLP_PARAMS 18817
+/* packed inference form: BF16 W1^T, W2^T in the tensor cores' layout + FP32 biases */
+#define RPCA_MLP_PACKED_BYTES 38416
+
+/* Features of the columns of dense A (m x n, lda >= n, device) into F (n x 16,
+ * device).  ws: rpca_features_workspace_size(m, n) bytes, 256-byte aligned. */
+size_t rpca_features_workspace_size(int64_t m, int64_t n);
+int rpca_sketch_features(const float *A, int64_t m, int64_t n, int64_t lda, int32_t raw, uint64_t seed,
+                         float *F, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* Features of every matrix of a batch (descs: device array as for rpca_batched;
+ * only A, m, n, lda are read).  The columns of item i go to rows
+ * col_offsets[i] .. col_offsets[i] + n_i - 1 of F (col_offsets: count int64
+ * values, device).  Items with A null, m < 1, n < 1 or lda < n are skipped. */
+int rpca_batched_features(int32_t count, const rpca_mat_desc *descs, int32_t raw, uint64_t seed,
+                          const int64_t *col_offsets, float *F, rpca_stream_t stream);
+
+/* FP32 parameters -> packed inference form (RPCA_MLP_PACKED_BYTES, 16-byte
+ * aligned, device). */
+int rpca_mlp_pack(const float *params, void *packed, rpca_stream_t stream);
+
+/* Inference on the tcgen05 tensor cores (BF16 operands, FP32 accumulation):
+ * for N feature rows F (N x 16), y (N) = the MLP output and d (N) = the
+ * weights clip(exp(y), 1e-2, 1e2); either output may be NULL.
+ * ws: rpca_mlp_forward_workspace_size() bytes (the status word). */
+size_t rpca_mlp_forward_workspace_size(void);
+int rpca_mlp_forward(const void *packed, const float *F, int64_t N, float *y, float *d, void *ws,
+                     size_t ws_bytes, rpca_stream_t stream);
+
+/* Training step pieces (FP32): loss = mean_j (y_j - t_j)^2 over the N rows of
+ * F with targets t (N), and grad (RPCA_MLP_PARAMS) = d loss / d params; loss
+ * may be NULL.  ws: rpca_mlp_grad_workspace_size(N) bytes.  Deterministic. */
+size_t rpca_mlp_grad_workspace_size(int64_t N);
+int rpca_mlp_loss_grad(const float *params, const float *F, const float *t, int64_t N, float *grad,
+                       float *loss, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* Adam (Kingma & Ba 2015) with bias correction, step >= 1: m1, m2 are the
+ * moment buffers (RPCA_MLP_PARAMS each, zero before step 1), updated in place
+ * with params. */
+int rpca_mlp_adam(float *params, const float *grad, float *m1, float *m2, int32_t step, float lr,
+                  float beta1, float beta2, float eps, rpca_stream_t stream);
+
+/* Training targets from right singular vectors V (n x >= k, ldv, device):
+ * t_j = log(n |V[j, 0:k]|^2 / k + 1e-3) (t: n values, device). */
+int rpca_leverage_target(const float *V, int64_t n, int64_t ldv, int32_t k, float *t, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Dense randomized PCA with the learned sketch and its fallback:
+ *   features -> MLP -> d; rpca_dense with diag(d) Omega; the residual
+ *   estimate of Section 4 (resid_iters power iterations, start from the
+ *   stream (seed, 1)); if l > k and the estimate exceeds
+ *   fallback_ratio * s_{k+1}, where s_{k+1} is the (k+1)-th singular value
+ *   of the rank-l approximation, rpca_dense runs again with the plain Omega
+ *   and the call returns RPCA_FELL_BACK; otherwise RPCA_OK (positive device
+ *   notes of the inner runs, such as a shifted CholeskyQR, are not returned).
+ * o->omega and o->col_weights must be NULL.  mlp_packed: rpca_mlp_pack output.
+ * est_out (host, 2 doubles, may be NULL): the estimate for the learned run and
+ * s_{k+1} (0 when l == k).  Waits for `stream` (the comparison is on the host).
+ * ws: rpca_dense_learned_workspace_size(m, n, o) bytes, 256-byte aligned.
+ * ---------------------------------------------------------------------- */
+size_t rpca_dense_learned_workspace_size(int64_t m, int64_t n, const rpca_opts *o);
+int rpca_dense_learned(const float *A, int64_t m, int64_t n, int64_t lda, const rpca_opts *o,
+                       const void *mlp_packed, int32_t resid_iters, double fallback_ratio, float *U,
+                       int64_t ldu, float *S, float *V, int64_t ldv, double *est_out, void *ws,
+                       size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * The sketch's test matrix alone (Section 2; the step every call starts with).
  * Writes Omega (n x l, row-major, leading dimension ldo >= l, device): entry
  * (i, j) is element e = i*l + j of the stream in which Philox4x64-10 block b

@@ -28,7 +28,10 @@ coarse sketch.  This module restates, in plain numpy FP64:
   (hand-derived backpropagation);
 * the label: t_j = log(n l_j / k + 1e-3) with l_j = |V_k[j, :]|^2 the
   leverage of column j in the top-k right singular subspace;
-* the weight: d_j = clip(exp(y_j), 1e-2, 1e2).
+* the weight: d_j = clip(exp(y_j), 1e-2, 1e2);
+* forward_bf16: the same forward with the inference kernel's rounding points
+  (features, W1, W2 and h1 rounded to BF16 by round-to-nearest-even of the
+  FP32 value, biases and w3 in FP32), everything else in FP64.
 """
 from __future__ import annotations
 
@@ -118,6 +121,26 @@ def loss_grad(p: np.ndarray, F: np.ndarray, t: np.ndarray):
     db1 = dz1.sum(axis=0)
     g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
     return loss, g
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to BF16 (8 significant bits) by round-to-nearest-even of the FP32 value;
+    returned as FP64.  Finite inputs only."""
+    x32 = np.asarray(x, dtype=np.float32)
+    bits = x32.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    r = ((bits + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def forward_bf16(p: np.ndarray, F: np.ndarray) -> np.ndarray:
+    """MLP output with the tensor-core kernel's rounding points (module docstring)."""
+    W1, b1, W2, b2, w3, b3 = split_params(p)
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)   # noqa: E731
+    z1 = bf16_round(F) @ bf16_round(W1) + f32(b1)
+    h1 = bf16_round(np.maximum(f32(z1), 0.0))
+    z2 = h1 @ bf16_round(W2) + f32(b2)
+    return np.maximum(z2, 0.0) @ f32(w3) + f32(b3)
 
 
 def leverage_target(V: np.ndarray, k: int) -> np.ndarray:

@@ -18,6 +18,10 @@ RPCA_ERR_TIMEOUT = -6
 RPCA_ERR_UNSUPPORTED = -7
 RPCA_MAX_L = 224
 RPCA_NOALLOC_SCRATCH_BYTES = 64 << 20
+RPCA_MLP_FEATURES = 16
+RPCA_MLP_HIDDEN = 128
+RPCA_MLP_PARAMS = 18817
+RPCA_MLP_PACKED_BYTES = 38416
 
 PREC = {"fp32": 0, "bf16x3": 1}
 RENORM = {"cholqr": 0, "lu": 1}
@@ -51,6 +55,19 @@ SIGNATURES = [
                                       _P, _P, _SZ, _P]),
     ("rpca_batched_workspace_size", _SZ, [_I32, _I64, _I64, _OPTS]),
     ("rpca_batched", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P]),
+    ("rpca_features_workspace_size", _SZ, [_I64, _I64]),
+    ("rpca_sketch_features", C.c_int, [_P, _I64, _I64, _I64, _I32, _U64, _P, _P, _SZ, _P]),
+    ("rpca_batched_features", C.c_int, [_I32, _P, _I32, _U64, _P, _P, _P]),
+    ("rpca_mlp_pack", C.c_int, [_P, _P, _P]),
+    ("rpca_mlp_forward_workspace_size", _SZ, []),
+    ("rpca_mlp_forward", C.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    ("rpca_mlp_grad_workspace_size", _SZ, [_I64]),
+    ("rpca_mlp_loss_grad", C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    ("rpca_mlp_adam", C.c_int, [_P, _P, _P, _P, _I32, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+    ("rpca_leverage_target", C.c_int, [_P, _I64, _I64, _I32, _P, _P]),
+    ("rpca_dense_learned_workspace_size", _SZ, [_I64, _I64, _OPTS]),
+    ("rpca_dense_learned", C.c_int, [_P, _I64, _I64, _I64, _OPTS, _P, _I32, C.c_double, _P, _I64, _P, _P, _I64,
+                                     C.POINTER(C.c_double), _P, _SZ, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),

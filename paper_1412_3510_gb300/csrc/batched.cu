@@ -14,6 +14,7 @@
 // (l <= 32) are done by warps in shared memory.  Products stream A through
 // shared-memory tiles with FP32 FFMA.
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace rpca {
 
@@ -57,37 +58,16 @@ struct Smem {
 };
 
 // ---------------------------------------------------------------------------
-// Philox4x64-10 (same mapping as the single-matrix path: element e = i*l + j of
-// the stream keyed (seed, 0), Box-Muller on (top 23 bits + 1/2) / 2^23)
+// Test matrix of one item: the single-matrix path's stream keyed (seed, 0), element
+// e = i*l + j, scaled by the optional column weights.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void philox(uint64_t c0, uint64_t k0, uint64_t k1, uint64_t (&w)[4]) {
-    uint64_t c1 = 0, c2 = 0, c3 = 0;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k0 += 0x9E3779B97F4A7C15ull; k1 += 0xBB67AE8584CAA73Bull; }
-        const uint64_t hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c0), lo0 = 0xD2E7470EE14C6C93ull * c0;
-        const uint64_t hi1 = __umul64hi(0xCA5A826395121157ull, c2), lo1 = 0xCA5A826395121157ull * c2;
-        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    }
-    w[0] = c0; w[1] = c1; w[2] = c2; w[3] = c3;
-}
-__device__ __forceinline__ float u23(uint64_t w) { return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1p-23f; }
-
 __device__ void gen_omega(Smem &sm, int64_t n, int l, int lp, uint64_t seed, const float *weights) {
     for (int64_t e = threadIdx.x; e < n * lp; e += blockDim.x) sm.X[e] = 0.f;
     __syncthreads();
     const int64_t total = n * (int64_t)l, nblk = (total + 3) / 4;
     for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) {
-        uint64_t w[4];
-        philox((uint64_t)b, seed, 0, w);
-        float z[4], sn, cs;
-        float r = sqrtf(-2.0f * logf(u23(w[0])));
-        sincospif(2.0f * u23(w[1]), &sn, &cs);
-        z[0] = r * cs; z[1] = r * sn;
-        r = sqrtf(-2.0f * logf(u23(w[2])));
-        sincospif(2.0f * u23(w[3]), &sn, &cs);
-        z[2] = r * cs; z[3] = r * sn;
+        float z[4];
+        gauss4((uint64_t)b, seed, 0, z);
         for (int t = 0; t < 4; ++t) {
             const int64_t e = 4 * b + t;
             if (e < total) {

@@ -72,6 +72,20 @@ extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, con
     return rpca::run_pipeline(op, o, U, ldu, S, V, ldv, ws, L, (cudaStream_t)stream);
 }
 
+namespace rpca {
+
+// Byte offset, within rpca_dense's workspace, of the l singular values of the
+// small SVD (descending), valid after rpca_dense has run with the same arguments.
+size_t dense_sigma_offset(int64_t m, int64_t n, const float *A, int64_t lda, const rpca_opts *o) {
+    DenseOp op;
+    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
+    const int lp = padded_l(o->l);
+    const int splits = std::max(choose_splits(n, lp, m), tc_adjoint_splits(n, m, lp));
+    return make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp)).sig;
+}
+
+}  // namespace rpca
+
 extern "C" size_t rpca_resid_workspace_size(int64_t m, int64_t n, int32_t k) {
     if (m < 1 || n < 1 || k < 0 || k > RPCA_MAX_L) return 0;
     return rpca::make_resid_layout(m, n, k, rpca::choose_splits(n, 8, m)).total;

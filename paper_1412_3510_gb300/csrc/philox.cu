@@ -3,38 +3,11 @@
 // Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3"
 // (SC'11), followed by the Box-Muller transform in FP32.
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace rpca {
 
 namespace {
-
-constexpr uint64_t kM0 = 0xD2E7470EE14C6C93ull;   // Philox4x64 multipliers
-constexpr uint64_t kM1 = 0xCA5A826395121157ull;
-constexpr uint64_t kW0 = 0x9E3779B97F4A7C15ull;   // Weyl key increments
-constexpr uint64_t kW1 = 0xBB67AE8584CAA73Bull;
-
-struct Block4 { uint64_t w[4]; };
-
-__device__ __forceinline__ Block4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
-                                                uint64_t c3, uint64_t k0, uint64_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k0 += kW0; k1 += kW1; }
-        const uint64_t hi0 = __umul64hi(kM0, c0), lo0 = kM0 * c0;
-        const uint64_t hi1 = __umul64hi(kM1, c2), lo1 = kM1 * c2;
-        const uint64_t n0 = hi1 ^ c1 ^ k0;
-        const uint64_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    }
-    Block4 b;
-    b.w[0] = c0; b.w[1] = c1; b.w[2] = c2; b.w[3] = c3;
-    return b;
-}
-
-// (top 23 bits + 1/2) / 2^23: exact in FP32, strictly inside (0, 1).
-__device__ __forceinline__ float uniform23(uint64_t w) {
-    return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1p-23f;
-}
 
 __global__ void omega_kernel(int64_t n, int l, uint64_t seed, uint64_t stream_id,
                              const float *__restrict__ weights, float *__restrict__ out,
@@ -43,20 +16,8 @@ __global__ void omega_kernel(int64_t n, int l, uint64_t seed, uint64_t stream_id
     const int64_t nblk = (total + 3) / 4;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
          b += (int64_t)gridDim.x * blockDim.x) {
-        const Block4 x = philox4x64_10((uint64_t)b, 0, 0, 0, seed, stream_id);
         float z[4];
-        {
-            const float r = sqrtf(-2.0f * logf(uniform23(x.w[0])));
-            float sn, cs;
-            sincospif(2.0f * uniform23(x.w[1]), &sn, &cs);
-            z[0] = r * cs; z[1] = r * sn;
-        }
-        {
-            const float r = sqrtf(-2.0f * logf(uniform23(x.w[2])));
-            float sn, cs;
-            sincospif(2.0f * uniform23(x.w[3]), &sn, &cs);
-            z[2] = r * cs; z[3] = r * sn;
-        }
+        gauss4((uint64_t)b, seed, stream_id, z);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int64_t e = 4 * b + t;
@@ -75,9 +36,10 @@ __global__ void philox_raw_kernel(uint64_t k0, uint64_t k1, uint64_t first, int6
                                   uint64_t *__restrict__ out) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks;
          b += (int64_t)gridDim.x * blockDim.x) {
-        const Block4 x = philox4x64_10(first + (uint64_t)b, 0, 0, 0, k0, k1);
+        uint64_t w[4];
+        philox4x64_10(first + (uint64_t)b, k0, k1, w);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) out[4 * b + t] = x.w[t];
+        for (int t = 0; t < 4; ++t) out[4 * b + t] = w[t];
     }
 }
 

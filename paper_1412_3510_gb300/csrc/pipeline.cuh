@@ -40,4 +40,7 @@ int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status = true);
 
+// Offset of the small SVD's singular values in rpca_dense's workspace.
+size_t dense_sigma_offset(int64_t m, int64_t n, const float *A, int64_t lda, const rpca_opts *o);
+
 }  // namespace rpca

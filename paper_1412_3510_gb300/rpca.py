@@ -342,3 +342,142 @@ def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = F
     if check:
         _check(rpca_read_status(ws, stream), "rpca_batched (device)")
     return batch.U, batch.S, batch.V
+
+
+# ---------------------------------------------------------------------------
+# learned sketch weighting
+# ---------------------------------------------------------------------------
+def rpca_sketch_features(A: torch.Tensor, raw: bool = False, seed: int = 0, F: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The n x 16 column features of dense A (see include/rpca.h)."""
+    _need_cuda(A, "A")
+    lda = _rowmajor_ld(A, "A")
+    m, n = A.shape
+    lib = L.load()
+    need = int(lib.rpca_features_workspace_size(m, n))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_features_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if F is None:
+        F = torch.empty(n, L.RPCA_MLP_FEATURES, dtype=torch.float32, device=A.device)
+    _check(lib.rpca_sketch_features(_ptr(A), m, n, lda, int(bool(raw)), int(seed) & ((1 << 64) - 1), _ptr(F),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "rpca_sketch_features")
+    return F
+
+
+def batch_col_offsets(batch: "Batch") -> tuple[torch.Tensor, int]:
+    """(device int64 offsets of each item's first column, total columns)."""
+    ns = [int(a.shape[1]) for a in batch.mats]
+    offs = [0]
+    for n in ns[:-1]:
+        offs.append(offs[-1] + n)
+    return torch.tensor(offs, dtype=torch.int64, device=batch.desc.device), sum(ns)
+
+
+def rpca_batched_features(batch: "Batch", raw: bool = False, seed: int = 0, col_offsets=None,
+                          F: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Features of every matrix of `batch`, stacked (sum n_i) x 16 in item order."""
+    if col_offsets is None:
+        col_offsets, total = batch_col_offsets(batch)
+    else:
+        total = sum(int(a.shape[1]) for a in batch.mats)
+    if F is None:
+        F = torch.empty(total, L.RPCA_MLP_FEATURES, dtype=torch.float32, device=batch.desc.device)
+    _check(L.load().rpca_batched_features(len(batch.mats), _ptr(batch.desc), int(bool(raw)),
+                                          int(seed) & ((1 << 64) - 1), _ptr(col_offsets), _ptr(F),
+                                          _stream(stream)), "rpca_batched_features")
+    return F
+
+
+def rpca_mlp_pack(params: torch.Tensor, packed: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """FP32 parameters (RPCA_MLP_PARAMS) -> the packed inference blob (uint8 tensor)."""
+    _need_cuda(params, "params")
+    if params.numel() != L.RPCA_MLP_PARAMS or not params.is_contiguous():
+        raise ValueError("params must be a contiguous vector of RPCA_MLP_PARAMS floats")
+    if packed is None:
+        packed = torch.empty(L.RPCA_MLP_PACKED_BYTES, dtype=torch.uint8, device=params.device)
+    _check(L.load().rpca_mlp_pack(_ptr(params), _ptr(packed), _stream(stream)), "rpca_mlp_pack")
+    return packed
+
+
+def rpca_mlp_forward(packed: torch.Tensor, F: torch.Tensor, want_y: bool = True, want_d: bool = True,
+                     ws: torch.Tensor | None = None, stream=None, check: bool = True):
+    """(y, d) for the rows of F (N x 16) on the tensor cores; either may be None."""
+    _need_cuda(F, "F")
+    if F.dim() != 2 or F.shape[1] != L.RPCA_MLP_FEATURES or not F.is_contiguous():
+        raise ValueError("F must be a contiguous N x 16 tensor")
+    N = F.shape[0]
+    y = torch.empty(N, dtype=torch.float32, device=F.device) if want_y else None
+    d = torch.empty(N, dtype=torch.float32, device=F.device) if want_d else None
+    lib = L.load()
+    if ws is None:
+        ws = workspace(int(lib.rpca_mlp_forward_workspace_size()), F.device)
+    _check(lib.rpca_mlp_forward(_ptr(packed), _ptr(F), N, _ptr(y), _ptr(d), _ptr(ws), ws.numel(),
+                                _stream(stream)), "rpca_mlp_forward")
+    if check:
+        _check(rpca_read_status(ws, stream), "rpca_mlp_forward (device)")
+    return y, d
+
+
+def rpca_mlp_loss_grad(params: torch.Tensor, F: torch.Tensor, t: torch.Tensor, grad: torch.Tensor | None = None,
+                       loss: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """(loss tensor [1], grad tensor [RPCA_MLP_PARAMS]) of the mean squared error."""
+    for x, nm in ((params, "params"), (F, "F"), (t, "t")):
+        _need_cuda(x, nm)
+        if not x.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+    N = F.shape[0]
+    lib = L.load()
+    need = int(lib.rpca_mlp_grad_workspace_size(N))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, F.device)
+    if grad is None:
+        grad = torch.empty(L.RPCA_MLP_PARAMS, dtype=torch.float32, device=F.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=F.device)
+    _check(lib.rpca_mlp_loss_grad(_ptr(params), _ptr(F), _ptr(t), N, _ptr(grad), _ptr(loss), _ptr(ws), ws.numel(),
+                                  _stream(stream)), "rpca_mlp_loss_grad")
+    return loss, grad
+
+
+def rpca_mlp_adam(params, grad, m1, m2, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None) -> None:
+    _check(L.load().rpca_mlp_adam(_ptr(params), _ptr(grad), _ptr(m1), _ptr(m2), int(step), float(lr), float(beta1),
+                                  float(beta2), float(eps), _stream(stream)), "rpca_mlp_adam")
+
+
+def rpca_leverage_target(V: torch.Tensor, k: int, t: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _need_cuda(V, "V")
+    ldv = _rowmajor_ld(V, "V")
+    n = V.shape[0]
+    if t is None:
+        t = torch.empty(n, dtype=torch.float32, device=V.device)
+    _check(L.load().rpca_leverage_target(_ptr(V), n, ldv, int(k), _ptr(t), _stream(stream)), "rpca_leverage_target")
+    return t
+
+
+def rpca_dense_learned(A: torch.Tensor, packed: torch.Tensor, k: int, l: int | None = None, its: int = 2,
+                       raw: bool = False, seed: int = 0, precision: str = "fp32", resid_iters: int = 8,
+                       fallback_ratio: float = 1.1, ws: torch.Tensor | None = None, stream=None):
+    """Learned-sketch PCA with fallback.  Returns (U, S, V, info) with info =
+    {"fell_back": bool, "est": residual estimate of the learned run, "s_k1": s_{k+1}}."""
+    _need_cuda(A, "A")
+    lda = _rowmajor_ld(A, "A")
+    m, n = A.shape
+    opts = make_opts(k, l, its, raw, seed, precision, "cholqr")
+    lib = L.load()
+    need = int(lib.rpca_dense_learned_workspace_size(m, n, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_dense_learned_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    U = torch.empty(m, k, dtype=torch.float32, device=A.device)
+    S = torch.empty(k, dtype=torch.float32, device=A.device)
+    V = torch.empty(n, k, dtype=torch.float32, device=A.device)
+    est = (C.c_double * 2)()
+    code = lib.rpca_dense_learned(_ptr(A), m, n, lda, C.byref(opts), _ptr(packed), int(resid_iters),
+                                  float(fallback_ratio), _ptr(U), k, _ptr(S), _ptr(V), k, est, _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check(code, "rpca_dense_learned")
+    return U, S, V, {"fell_back": code == L.RPCA_FELL_BACK, "est": est[0], "s_k1": est[1]}

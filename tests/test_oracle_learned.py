@@ -77,3 +77,26 @@ def test_adam_step_decreases_loss():
         _, g = L.loss_grad(p, F, t)
         p, m1, m2 = L.adam_step(p, g, m1, m2, step, 1e-3)
     assert L.loss_grad(p, F, t)[0] < 0.2 * l0
+
+
+def test_bf16_round_ties_and_library():
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to the even mantissa (1)
+    assert L.bf16_round(1 + 2.0 ** -8) == 1.0
+    # 1 + 3 * 2^-8 is halfway between 1 + 2^-7 (odd) and 1 + 2^-6 (even)
+    assert L.bf16_round(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+    assert L.bf16_round(1 + 2.0 ** -8 + 2.0 ** -20) == 1 + 2.0 ** -7
+    assert L.bf16_round(-3.0) == -3.0 and L.bf16_round(0.0) == 0.0
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(5).standard_normal(10000).astype(np.float32) * 10.0
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(L.bf16_round(x), ref)
+
+
+def test_forward_bf16_close_to_exact():
+    p = L.init_params(4)
+    F = np.random.default_rng(6).standard_normal((300, L.F_IN))
+    y, _ = L.forward(p, F)
+    yb = L.forward_bf16(p, F)
+    # BF16 keeps 8 bits: the outputs agree to a few parts in 1e3 of their scale
+    assert np.max(np.abs(y - yb)) < 0.02 * max(1.0, np.max(np.abs(y)))
+    assert not np.array_equal(y, yb)
