@@ -359,6 +359,8 @@ def run_batched(args, w, dev, world, rank, barrier):
                "h2d_bytes_per_step": int(4 * mn), "d2h_bytes_per_step": int(sum(u.numel() * 4 for u in batch.U))}
         del hosts, outs
 
+    learned = None if args.no_learned else learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -387,8 +389,106 @@ def run_batched(args, w, dev, world, rank, barrier):
                      "resid_over_sigma_k1_max": float(ratios.max()),
                      "fraction_resid_ok": float(np.mean(ratios <= 1.1)), "status": status, "bad_items": item_bad},
         "clocks": sampler.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "learned_sketch": learned,
     }
     print(json.dumps(line), flush=True)
+
+
+def learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream):
+    """Learned vs plain test matrix on the same batch: train the weighting MLP on a
+    separate set of matrices from the same family (labels from the plain method with
+    l = k + 16, its = 4), then compare residual / sigma_{k+1} on a fixed sample and
+    time features + MLP + batched PCA as one CUDA graph."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1412_3510_gb300 as rp
+    from paper_1412_3510_gb300 import learned as LR
+    from paper_1412_3510_gb300 import _lib as LIB
+
+    k, l, raw = w["k"], w["l"], w["raw"]
+    seed = 1 + rank
+    # training family: same law as the batch, disjoint seeds; labels from the plain
+    # batched method at the widest sketch its per-CTA buffer holds for n <= 1024
+    l_label = 23
+    tr_specs = synth.kernel_batch_specs(args.learned_train, w["seed"] + 7919 + rank, w["m_range"], w["n_range"])
+    params, packed, info = LR.train_sketch_mlp_family(lambda sp: synth.kernel_matrix_torch(sp, dev), tr_specs, k,
+                                                      l_label=l_label, its_label=6, raw=raw,
+                                                      steps=args.learned_steps, batch=4096, lr=1e-3, seed=11)
+    torch.cuda.empty_cache()
+    fws = rp.workspace(int(LIB.load().rpca_batched_features_workspace_size(batch.max_m)), dev)
+
+    offs, total = rp.batch_col_offsets(batch)
+    Fbuf = torch.empty(total, LIB.RPCA_MLP_FEATURES, dtype=torch.float32, device=dev)
+    dbuf = torch.empty(total, dtype=torch.float32, device=dev)
+    mws = rp.workspace(int(LIB.load().rpca_mlp_forward_workspace_size()), dev)
+    views, o = [], 0
+    for a in mats:
+        views.append(dbuf[o:o + a.shape[1]])
+        o += a.shape[1]
+    wtab = rp.weights_table(views, dev)
+
+    def weights():
+        rp.rpca_batched_features(batch, raw=raw, seed=seed, col_offsets=offs, F=Fbuf, ws=fws)
+        rp.rpca_mlp_forward(packed, Fbuf, want_y=False, ws=mws, check=False, d=dbuf)
+
+    def step(its, learned):
+        if learned:
+            weights()
+        rp.rpca_batched(batch, l, its=its, raw=raw, seed=seed, col_weights=wtab if learned else None, ws=ws,
+                        check=False)
+
+    sample = list(range(0, len(mats), max(1, len(mats) // 64)))[:64]
+    sk1 = []
+    for i in sample:
+        a = mats[i].double()
+        ac = a - (0 if raw else a.mean(0))
+        sk1.append(float(torch.linalg.svdvals(ac)[k].item()))
+
+    def ratios():
+        r = [rp.rpca_resid_norm(mats[i], batch.U[i], batch.S[i], batch.V[i], raw=raw, iters=args.resid_iters,
+                                seed=7) / s1 for i, s1 in zip(sample, sk1)]
+        return np.array(r)
+
+    def summary(r):
+        return {"median": float(np.median(r)), "q90": float(np.quantile(r, 0.9)), "max": float(r.max()),
+                "fraction_ok": float(np.mean(r <= 1.1))}
+
+    steps = max(3, args.steps // 4)
+    acc, speed, launches = {}, {}, {}
+    for its in (1, 2):
+        for name, lrn in (("plain", False), ("learned", True)):
+            step(its, lrn)
+            bad = int((batch.status != 0).sum().item())
+            acc[f"{name}_its{its}"] = summary(ratios()) | {"bad_items": bad}
+            for _ in range(args.warmup):
+                step(its, lrn)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            c0 = rp.rpca_launch_count()
+            with torch.cuda.graph(g):
+                step(its, lrn)
+            launches[f"{name}_its{its}"] = rp.rpca_launch_count() - c0
+            ms = timed(g, steps) / steps
+            speed[f"{name}_its{its}"] = len(mats) / (ms / 1e3)
+            del g
+    for _ in range(args.warmup):
+        weights()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        weights()
+    w_ms = timed(g, steps) / steps
+    return {"train": {"matrices": info["matrices"], "skipped": info["skipped"], "columns": info["samples"],
+                      "steps": info["steps"], "batch": info["batch"], "train_seconds": info["seconds"],
+                      "label_seconds": info["label_seconds"],
+                      "label_run": f"plain batched, l={l_label}, its=6, chunks of 2048 matrices",
+                      "target_var": info["target_var"], "final_mse": info["final_mse"]},
+            "sample": len(sample), "resid_estimator": f"power method, {args.resid_iters} iterations",
+            "sigma_k1": "exact (FP64 svdvals of the centred matrix)",
+            "accuracy": acc, "pca_per_s": speed, "gpu_launches_per_step": launches,
+            "weights_ms_per_batch": w_ms,
+            "fallback": "dense entry point only (rpca_dense_learned); the batched form reports accuracy"}
 
 
 # ---------------------------------------------------------------------------
@@ -409,6 +509,9 @@ def main():
     ap.add_argument("--resid-iters", type=int, default=20)
     ap.add_argument("--ref-rows", type=int, default=50000)
     ap.add_argument("--ref-budget", type=float, default=150.0)
+    ap.add_argument("--no-learned", action="store_true", help="batched workloads: skip the learned-sketch A/B")
+    ap.add_argument("--learned-train", type=int, default=50000, help="training matrices for the learned sketch")
+    ap.add_argument("--learned-steps", type=int, default=6000, help="Adam steps for the learned sketch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -253,11 +253,14 @@ int rpca_sketch_features(const float *A, int64_t m, int64_t n, int64_t lda, int3
                          float *F, void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* Features of every matrix of a batch (descs: device array as for rpca_batched;
- * only A, m, n, lda are read).  The columns of item i go to rows
- * col_offsets[i] .. col_offsets[i] + n_i - 1 of F (col_offsets: count int64
- * values, device).  Items with A null, m < 1, n < 1 or lda < n are skipped. */
-int rpca_batched_features(int32_t count, const rpca_mat_desc *descs, int32_t raw, uint64_t seed,
-                          const int64_t *col_offsets, float *F, rpca_stream_t stream);
+ * only A, m, n, lda are read; max_m >= every m_i).  The columns of item i go to
+ * rows col_offsets[i] .. col_offsets[i] + n_i - 1 of F (col_offsets: count
+ * int64 values, device).  Items with A null, m < 1, n < 1, lda < n or
+ * m > max_m are skipped.  ws: rpca_batched_features_workspace_size(max_m)
+ * bytes, 256-byte aligned (holds G). */
+size_t rpca_batched_features_workspace_size(int64_t max_m);
+int rpca_batched_features(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int32_t raw, uint64_t seed,
+                          const int64_t *col_offsets, float *F, void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* FP32 parameters -> packed inference form (RPCA_MLP_PACKED_BYTES, 16-byte
  * aligned, device). */

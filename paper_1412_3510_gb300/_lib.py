@@ -57,7 +57,8 @@ SIGNATURES = [
     ("rpca_batched", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P]),
     ("rpca_features_workspace_size", _SZ, [_I64, _I64]),
     ("rpca_sketch_features", C.c_int, [_P, _I64, _I64, _I64, _I32, _U64, _P, _P, _SZ, _P]),
-    ("rpca_batched_features", C.c_int, [_I32, _P, _I32, _U64, _P, _P, _P]),
+    ("rpca_batched_features_workspace_size", _SZ, [_I64]),
+    ("rpca_batched_features", C.c_int, [_I32, _P, _I64, _I32, _U64, _P, _P, _P, _SZ, _P]),
     ("rpca_mlp_pack", C.c_int, [_P, _P, _P]),
     ("rpca_mlp_forward_workspace_size", _SZ, []),
     ("rpca_mlp_forward", C.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),

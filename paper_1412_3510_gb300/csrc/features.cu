@@ -13,9 +13,9 @@
 //   log((x_j^2 m + tau) / (q_j + tau)) / 4, S[0..7, j] / (rho_r + 1e-30),
 //   log(m) / 8, log(n) / 8, 0, 0, 0.
 // Dense A: a multi-CTA pass (column strips x row splits) and three small
-// finishing kernels.  Batched: one CTA per matrix, G drawn on the fly.
+// finishing kernels.  Batched: one CTA per matrix, every item reading the rows
+// of one G drawn for the largest m (G's rows do not depend on m).
 #include "internal.cuh"
-#include "philox.cuh"
 
 namespace rpca {
 
@@ -62,17 +62,16 @@ __device__ __forceinline__ void write_features(float *Fj, const ColStats &cs, fl
 }
 
 // ---------------------------------------------------------------------------
-// dense: pass over A
+// one 128-column strip over rows [r0, r1): lanes own 4 adjacent columns, the 8
+// warps take interleaved rows, 4 rows in flight per warp; per-warp partials to red
+// (kWarps x kQ x kStrip)
 // ---------------------------------------------------------------------------
 template <bool VEC>
-__global__ void __launch_bounds__(kThreads) feat_pass_kernel(const float *__restrict__ A, int64_t m, int64_t n,
-                                                             int64_t lda, int raw, const float *__restrict__ G,
-                                                             int64_t rows_per_split, float *__restrict__ part) {
-    extern __shared__ float red[];               // kWarps x kQ x kStrip
+__device__ __forceinline__ void strip_pass(const float *__restrict__ A, int64_t n, int64_t lda, int raw,
+                                           const float *__restrict__ G, int64_t cb, int64_t r0, int64_t r1,
+                                           float *red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t col0 = (int64_t)blockIdx.x * kStrip + 4 * lane;
-    const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
-    const int64_t r1 = min(m, r0 + rows_per_split);
+    const int64_t col0 = cb + 4 * lane;
     bool live[4];
     float shift[4], s1[4], s2[4], mx[4], mn[4], Sd[4][kSk];
 #pragma unroll
@@ -126,7 +125,6 @@ __global__ void __launch_bounds__(kThreads) feat_pass_kernel(const float *__rest
             }
         }
     }
-    // combine the warps (fixed order), write this split's partials
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         float *o = red + (warp * kQ) * kStrip + 4 * lane + q;
@@ -137,16 +135,34 @@ __global__ void __launch_bounds__(kThreads) feat_pass_kernel(const float *__rest
 #pragma unroll
         for (int r = 0; r < kSk; ++r) o[(4 + r) * kStrip] = Sd[q][r];
     }
+}
+
+// quantity qty of strip column c, combined over the warps in a fixed order
+__device__ __forceinline__ float strip_combine(const float *red, int qty, int c) {
+    float v = red[qty * kStrip + c];
+    for (int w = 1; w < kWarps; ++w) {
+        const float x = red[(w * kQ + qty) * kStrip + c];
+        v = qty == 2 ? fmaxf(v, x) : qty == 3 ? fminf(v, x) : v + x;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// dense: pass over A, grid = (column strips, row splits)
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) feat_pass_kernel(const float *__restrict__ A, int64_t m, int64_t n,
+                                                             int64_t lda, int raw, const float *__restrict__ G,
+                                                             int64_t rows_per_split, float *__restrict__ part) {
+    extern __shared__ float red[];               // kWarps x kQ x kStrip
+    const int64_t cb = (int64_t)blockIdx.x * kStrip;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_split;
+    strip_pass<VEC>(A, n, lda, raw, G, cb, r0, min(m, r0 + rows_per_split), red);
     __syncthreads();
     for (int e = threadIdx.x; e < kQ * kStrip; e += kThreads) {
         const int qty = e / kStrip, c = e % kStrip;
-        const int64_t col = (int64_t)blockIdx.x * kStrip + c;
-        float v = red[qty * kStrip + c];
-        for (int w = 1; w < kWarps; ++w) {
-            const float x = red[(w * kQ + qty) * kStrip + c];
-            v = qty == 2 ? fmaxf(v, x) : qty == 3 ? fminf(v, x) : v + x;
-        }
-        if (col < n) part[((int64_t)blockIdx.y * n + col) * kQ + qty] = v;
+        const int64_t col = cb + c;
+        if (col < n) part[((int64_t)blockIdx.y * n + col) * kQ + qty] = strip_combine(red, qty, c);
     }
 }
 
@@ -270,88 +286,58 @@ FeatPlan feat_plan(int64_t m, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------
-// batched: one CTA per matrix
+// batched: one CTA per matrix; G (max_m x 8) precomputed, shared by all items
 // ---------------------------------------------------------------------------
-constexpr int kBCols = 4;             // columns per thread per column block
-constexpr int kGRows = 64;            // G rows drawn per chunk
-
-__global__ void __launch_bounds__(kThreads) feat_batched_kernel(int count, const rpca_mat_desc *__restrict__ descs,
-                                                                int raw, uint64_t seed,
+__global__ void __launch_bounds__(kThreads, 2) feat_batched_kernel(int count, const rpca_mat_desc *__restrict__ descs,
+                                                                int raw, const float *__restrict__ G,
+                                                                int64_t max_m,
                                                                 const int64_t *__restrict__ col_offsets,
                                                                 float *__restrict__ F) {
-    __shared__ float g_s[kGRows * kSk];
-    __shared__ float gsum_s[kSk];
-    __shared__ float red[kWarps][1 + kSk];
+    extern __shared__ float red[];               // kWarps x kQ x kStrip
+    __shared__ float gpart[kThreads / kSk][kSk];
+    __shared__ float wred[kWarps][1 + kSk];
     __shared__ float tot[1 + kSk];
+    __shared__ float gsum_s[kSk];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int item = blockIdx.x; item < count; item += gridDim.x) {
         const rpca_mat_desc dsc = descs[item];
         const int64_t m = dsc.m, n = dsc.n, lda = dsc.lda;
-        if (!dsc.A || m < 1 || n < 1 || lda < n) continue;          // uniform across the CTA
+        if (!dsc.A || m < 1 || n < 1 || lda < n || m > max_m) continue;     // uniform across the CTA
         const float *A = dsc.A;
         float *Fi = F + col_offsets[item] * RPCA_MLP_FEATURES;
-        // pass 1 over the column blocks: statistics into F's rows; pass 2 writes features
+        // sum_i G[i, r] over this item's rows
+        {
+            const int r = tid % kSk, rr = tid / kSk;
+            float a = 0.f;
+            for (int64_t i = rr; i < m; i += kThreads / kSk) a += G[i * kSk + r];
+            gpart[rr][r] = a;
+            __syncthreads();
+            if (tid < kSk) {
+                float v = 0.f;
+                for (int w = 0; w < kThreads / kSk; ++w) v += gpart[w][tid];
+                gsum_s[tid] = v;
+            }
+            __syncthreads();
+        }
+        float g[kSk];
+#pragma unroll
+        for (int r = 0; r < kSk; ++r) g[r] = gsum_s[r];
+        const bool vec = (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && lda % 4 == 0;
         float qsum = 0.f, ssq[kSk];
 #pragma unroll
         for (int r = 0; r < kSk; ++r) ssq[r] = 0.f;
-        for (int64_t cb = 0; cb < n; cb += (int64_t)kThreads * kBCols) {
-            float shift[kBCols], s1[kBCols], s2[kBCols], mx[kBCols], mn[kBCols], Sd[kBCols][kSk];
-            bool live[kBCols];
-#pragma unroll
-            for (int q = 0; q < kBCols; ++q) {
-                const int64_t col = cb + tid + (int64_t)q * kThreads;
-                live[q] = col < n;
-                shift[q] = (!raw && live[q]) ? A[col] : 0.f;
-                s1[q] = s2[q] = 0.f;
-                mx[q] = -INFINITY;
-                mn[q] = INFINITY;
-#pragma unroll
-                for (int r = 0; r < kSk; ++r) Sd[q][r] = 0.f;
-            }
-            if (tid < kSk && cb == 0) gsum_s[tid] = 0.f;     // sum_i G[i, r]: first column block only
-            for (int64_t i0 = 0; i0 < m; i0 += kGRows) {
-                const int nr = (int)(m - i0 < kGRows ? m - i0 : kGRows);
-                __syncthreads();
-                // element e = i * 8 + r of the stream (seed, 2): blocks 2 i and 2 i + 1
-                if (tid < 2 * nr) {
-                    float z[4];
-                    gauss4((uint64_t)(2 * i0 + tid), seed, 2, z);
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) g_s[tid * 4 + t] = z[t];
-                }
-                __syncthreads();
-                if (tid < kSk && cb == 0) {
-                    float a = 0.f;
-                    for (int i = 0; i < nr; ++i) a += g_s[i * kSk + tid];
-                    gsum_s[tid] += a;
-                }
-                for (int i = 0; i < nr; ++i) {
-                    const float *row = A + (i0 + i) * lda + cb + tid;
-                    float a[kBCols];
-#pragma unroll
-                    for (int q = 0; q < kBCols; ++q) a[q] = live[q] ? __ldg(row + q * kThreads) : 0.f;
-#pragma unroll
-                    for (int q = 0; q < kBCols; ++q) {
-                        if (!live[q]) continue;
-                        const float d = a[q] - shift[q];
-                        s1[q] += d;
-                        s2[q] = fmaf(d, d, s2[q]);
-                        mx[q] = fmaxf(mx[q], a[q]);
-                        mn[q] = fminf(mn[q], a[q]);
-#pragma unroll
-                        for (int r = 0; r < kSk; ++r) Sd[q][r] = fmaf(g_s[i * kSk + r], d, Sd[q][r]);
-                    }
-                }
-            }
+        for (int64_t cb = 0; cb < n; cb += kStrip) {
+            if (vec) strip_pass<true>(A, n, lda, raw, G, cb, 0, m, red);
+            else strip_pass<false>(A, n, lda, raw, G, cb, 0, m, red);
             __syncthreads();
-            float g[kSk];
+            const int64_t col = cb + tid;
+            if (tid < kStrip && col < n) {
+                float Sd[kSk];
 #pragma unroll
-            for (int r = 0; r < kSk; ++r) g[r] = gsum_s[r];
-#pragma unroll
-            for (int q = 0; q < kBCols; ++q) {
-                if (!live[q]) continue;
-                const int64_t col = cb + tid + (int64_t)q * kThreads;
-                const ColStats cs = finish_column(shift[q], s1[q], s2[q], mx[q], mn[q], Sd[q], g, m, raw);
+                for (int r = 0; r < kSk; ++r) Sd[r] = strip_combine(red, 4 + r, tid);
+                const ColStats cs = finish_column(raw ? 0.f : A[col], strip_combine(red, 0, tid),
+                                                  strip_combine(red, 1, tid), strip_combine(red, 2, tid),
+                                                  strip_combine(red, 3, tid), Sd, g, m, raw);
                 float *Fj = Fi + col * RPCA_MLP_FEATURES;
                 Fj[0] = cs.q;
                 Fj[1] = cs.c;
@@ -362,6 +348,7 @@ __global__ void __launch_bounds__(kThreads) feat_batched_kernel(int count, const
 #pragma unroll
                 for (int r = 0; r < kSk; ++r) ssq[r] = fmaf(cs.S[r], cs.S[r], ssq[r]);
             }
+            __syncthreads();
         }
         // CTA totals: qbar and rho
         {
@@ -373,13 +360,13 @@ __global__ void __launch_bounds__(kThreads) feat_batched_kernel(int count, const
             for (int e = 0; e <= kSk; ++e) {
 #pragma unroll
                 for (int o = 16; o; o >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
-                if (lane == 0) red[warp][e] = v[e];
+                if (lane == 0) wred[warp][e] = v[e];
             }
         }
         __syncthreads();
         if (tid <= kSk) {
             float v = 0.f;
-            for (int w = 0; w < kWarps; ++w) v += red[w][tid];
+            for (int w = 0; w < kWarps; ++w) v += wred[w][tid];
             v /= (float)n;
             tot[tid] = tid == 0 ? v : sqrtf(v);
         }
@@ -455,12 +442,27 @@ extern "C" int rpca_sketch_features(const float *A, int64_t m, int64_t n, int64_
     return launch_features(A, m, n, lda, raw ? 1 : 0, seed, F, ws, s);
 }
 
-extern "C" int rpca_batched_features(int32_t count, const rpca_mat_desc *descs, int32_t raw, uint64_t seed,
-                                     const int64_t *col_offsets, float *F, rpca_stream_t stream) {
-    if (count < 0 || (count > 0 && (!descs || !col_offsets || !F))) return RPCA_ERR_INVALID_ARG;
+extern "C" size_t rpca_batched_features_workspace_size(int64_t max_m) {
+    if (max_m < 1) return 0;
+    return ((size_t)max_m * kSk * sizeof(float) + 255) & ~(size_t)255;
+}
+
+extern "C" int rpca_batched_features(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int32_t raw,
+                                     uint64_t seed, const int64_t *col_offsets, float *F, void *ws, size_t ws_bytes,
+                                     rpca_stream_t stream) {
+    if (count < 0 || max_m < 1 || (count > 0 && (!descs || !col_offsets || !F))) return RPCA_ERR_INVALID_ARG;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < rpca_batched_features_workspace_size(max_m))
+        return RPCA_ERR_WORKSPACE;
     if (count == 0) return RPCA_OK;
-    const int grid = std::min<int>(count, 4 * num_sms());
-    feat_batched_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(count, descs, raw ? 1 : 0, seed, col_offsets, F);
+    cudaStream_t s = (cudaStream_t)stream;
+    float *G = static_cast<float *>(ws);
+    RPCA_TRY(launch_omega(max_m, kSk, seed, 2, nullptr, G, kSk, s));
+    const size_t smem = (size_t)kWarps * kQ * kStrip * sizeof(float);
+    if (cudaFuncSetAttribute(feat_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return RPCA_ERR_CUDA;
+    const int grid = std::min<int>(count, 2 * num_sms());
+    feat_batched_kernel<<<grid, kThreads, smem, s>>>(count, descs, raw ? 1 : 0, G, max_m, col_offsets, F);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

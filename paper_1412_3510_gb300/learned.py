@@ -1,6 +1,6 @@
 """Training driver for the learned sketch weighting.
 
-Labels come from the method itself: the plain batched PCA with a wider sketch
+Labels come from the method itself: the plain PCA with a wider sketch
 and more power iterations (Section 5's accuracy grows with both) gives V_k for
 each training matrix, and rpca_leverage_target turns V_k into the log relative
 leverage t_j = log(n |V_k[j, :]|^2 / k + 1e-3) that the MLP learns to predict
@@ -15,7 +15,7 @@ import time
 import torch
 
 from . import _lib as L
-from .rpca import (Batch, batch_col_offsets, rpca_batched, rpca_batched_features, rpca_gaussian_omega,
+from .rpca import (Batch, batch_col_offsets, rpca_batched_features, rpca_dense, rpca_gaussian_omega,
                    rpca_leverage_target, rpca_mlp_adam, rpca_mlp_loss_grad, rpca_mlp_pack, workspace)
 
 F_IN, H = L.RPCA_MLP_FEATURES, L.RPCA_MLP_HIDDEN
@@ -35,16 +35,51 @@ def init_params(seed: int = 0, device="cuda") -> torch.Tensor:
 
 def leverage_dataset(mats, k: int, l_label: int | None = None, its_label: int = 4, raw: bool = False,
                      seed: int = 0):
-    """(features (sum n_i) x 16, targets (sum n_i)) for a list of training matrices."""
+    """(features (sum n_i) x 16, targets (sum n_i)) for a list of training matrices.
+
+    The labelling runs use the dense entry point one matrix at a time (its sketch
+    width is not bounded by the batched kernel's per-CTA buffer)."""
+    ts = []
+    for a in mats:
+        l = min(l_label or k + 16, a.shape[0], a.shape[1])
+        _, _, V = rpca_dense(a, k, l, its=its_label, raw=raw, seed=seed + 1)
+        ts.append(rpca_leverage_target(V, k))
     batch = Batch(mats, k)
-    _, _, V = rpca_batched(batch, l=l_label or k + 16, its=its_label, raw=raw, seed=seed + 1)
-    t = torch.cat([rpca_leverage_target(v, k) for v in V])
     offs, _ = batch_col_offsets(batch)
     F = rpca_batched_features(batch, raw=raw, seed=seed, col_offsets=offs)
-    bad = int((batch.status != 0).sum().item())
-    if bad:
-        raise RuntimeError(f"{bad} training matrices failed in the labelling run")
-    return F, t
+    return F, torch.cat(ts)
+
+
+def leverage_dataset_family(make, specs, k: int, l_label: int, its_label: int = 6, raw: bool = False,
+                            seed: int = 0, chunk: int = 2048):
+    """(features, targets) over a large family of matrices, generated and labelled in
+    chunks: make(spec) returns one matrix on the device; each chunk is labelled by one
+    batched launch (sketch width l_label, its_label power iterations) and freed before
+    the next.  Matrices whose labelling run reports an error are left out.
+    Returns (F, t, info)."""
+    from .rpca import rpca_batched
+    Fs, ts = [], []
+    skipped = 0
+    for c0 in range(0, len(specs), chunk):
+        mats = [make(sp) for sp in specs[c0:c0 + chunk]]
+        batch = Batch(mats, k)
+        _, _, V = rpca_batched(batch, l=l_label, its=its_label, raw=raw, seed=seed + 1)
+        offs, _ = batch_col_offsets(batch)
+        F = rpca_batched_features(batch, raw=raw, seed=seed, col_offsets=offs)
+        ok = (batch.status == 0).cpu().tolist()
+        o = 0
+        for a, v, good in zip(mats, V, ok):
+            n = int(a.shape[1])
+            if good:
+                ts.append(rpca_leverage_target(v, k))
+                Fs.append(F[o:o + n])
+            else:
+                skipped += 1
+            o += n
+        Fs = [torch.cat(Fs)]
+        ts = [torch.cat(ts)]
+        del mats, batch, V, F
+    return Fs[0], ts[0], {"matrices": len(specs) - skipped, "skipped": skipped}
 
 
 def train_mlp(F: torch.Tensor, t: torch.Tensor, steps: int = 2000, batch: int = 4096, lr: float = 1e-3,
@@ -90,6 +125,22 @@ def train_sketch_mlp(mats, k: int, l_label: int | None = None, its_label: int = 
     params, info = train_mlp(F, t, steps=steps, batch=batch, lr=lr, seed=seed)
     info["label_seconds"] = t_label
     info["target_var"] = float(t.var().item())
+    return params, rpca_mlp_pack(params), info
+
+
+def train_sketch_mlp_family(make, specs, k: int, l_label: int, its_label: int = 6, raw: bool = False,
+                            steps: int = 6000, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+                            chunk: int = 2048):
+    """leverage_dataset_family, then training.  Returns (params, packed, info)."""
+    t0 = time.perf_counter()
+    F, t, dinfo = leverage_dataset_family(make, specs, k, l_label, its_label, raw, seed, chunk)
+    torch.cuda.synchronize(F.device)
+    t_label = time.perf_counter() - t0
+    params, info = train_mlp(F, t, steps=steps, batch=batch, lr=lr, seed=seed)
+    info |= dinfo
+    info["label_seconds"] = t_label
+    info["target_var"] = float(t.var().item())
+    info["final_mse"] = float(rpca_mlp_loss_grad(params, F[:65536].contiguous(), t[:65536].contiguous())[0].item())
     return params, rpca_mlp_pack(params), info
 
 

@@ -318,10 +318,17 @@ class Batch:
         self.status = torch.zeros(len(mats), dtype=torch.int32, device=device)
 
 
+def weights_table(col_weights, device) -> torch.Tensor:
+    """Device table of per-matrix weight pointers (0 for None) for rpca_batched; the
+    caller keeps the weight tensors alive while the table is in use."""
+    return torch.tensor([0 if w is None else w.data_ptr() for w in col_weights], dtype=torch.int64, device=device)
+
+
 def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
                  col_weights=None, ws: torch.Tensor | None = None, stream=None, check: bool = True):
-    """Randomized PCA of every matrix of `batch` in one launch.  col_weights: None or a
-    list of per-matrix n-vectors (or None entries).  Returns (U list, S list, V list)."""
+    """Randomized PCA of every matrix of `batch` in one launch.  col_weights: None, a
+    list of per-matrix n-vectors (or None entries), or a weights_table() tensor.
+    Returns (U list, S list, V list)."""
     k = batch.k
     opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr")
     lib = L.load()
@@ -332,9 +339,10 @@ def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = F
     if ws is None or ws.numel() < need:
         ws = workspace(need, batch.desc.device)
     wptr = None
-    if col_weights is not None:
-        wptr = torch.tensor([0 if w is None else w.data_ptr() for w in col_weights], dtype=torch.int64,
-                            device=batch.desc.device)
+    if isinstance(col_weights, torch.Tensor):
+        wptr = col_weights                    # a table from weights_table()
+    elif col_weights is not None:
+        wptr = weights_table(col_weights, batch.desc.device)
         batch._wkeep = (col_weights, wptr)
     code = lib.rpca_batched(count, _ptr(batch.desc), batch.max_m, batch.max_n, C.byref(opts), _ptr(wptr),
                             _ptr(batch.status), _ptr(ws), ws.numel(), _stream(stream))
@@ -376,7 +384,8 @@ def batch_col_offsets(batch: "Batch") -> tuple[torch.Tensor, int]:
 
 
 def rpca_batched_features(batch: "Batch", raw: bool = False, seed: int = 0, col_offsets=None,
-                          F: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                          F: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
     """Features of every matrix of `batch`, stacked (sum n_i) x 16 in item order."""
     if col_offsets is None:
         col_offsets, total = batch_col_offsets(batch)
@@ -384,9 +393,13 @@ def rpca_batched_features(batch: "Batch", raw: bool = False, seed: int = 0, col_
         total = sum(int(a.shape[1]) for a in batch.mats)
     if F is None:
         F = torch.empty(total, L.RPCA_MLP_FEATURES, dtype=torch.float32, device=batch.desc.device)
-    _check(L.load().rpca_batched_features(len(batch.mats), _ptr(batch.desc), int(bool(raw)),
-                                          int(seed) & ((1 << 64) - 1), _ptr(col_offsets), _ptr(F),
-                                          _stream(stream)), "rpca_batched_features")
+    lib = L.load()
+    need = int(lib.rpca_batched_features_workspace_size(batch.max_m))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, batch.desc.device)
+    _check(lib.rpca_batched_features(len(batch.mats), _ptr(batch.desc), batch.max_m, int(bool(raw)),
+                                     int(seed) & ((1 << 64) - 1), _ptr(col_offsets), _ptr(F), _ptr(ws),
+                                     ws.numel(), _stream(stream)), "rpca_batched_features")
     return F
 
 
@@ -402,14 +415,17 @@ def rpca_mlp_pack(params: torch.Tensor, packed: torch.Tensor | None = None, stre
 
 
 def rpca_mlp_forward(packed: torch.Tensor, F: torch.Tensor, want_y: bool = True, want_d: bool = True,
-                     ws: torch.Tensor | None = None, stream=None, check: bool = True):
-    """(y, d) for the rows of F (N x 16) on the tensor cores; either may be None."""
+                     ws: torch.Tensor | None = None, stream=None, check: bool = True, y=None, d=None):
+    """(y, d) for the rows of F (N x 16) on the tensor cores; either may be None.
+    y / d: optional preallocated outputs (N floats each)."""
     _need_cuda(F, "F")
     if F.dim() != 2 or F.shape[1] != L.RPCA_MLP_FEATURES or not F.is_contiguous():
         raise ValueError("F must be a contiguous N x 16 tensor")
     N = F.shape[0]
-    y = torch.empty(N, dtype=torch.float32, device=F.device) if want_y else None
-    d = torch.empty(N, dtype=torch.float32, device=F.device) if want_d else None
+    if y is None and want_y:
+        y = torch.empty(N, dtype=torch.float32, device=F.device)
+    if d is None and want_d:
+        d = torch.empty(N, dtype=torch.float32, device=F.device)
     lib = L.load()
     if ws is None:
         ws = workspace(int(lib.rpca_mlp_forward_workspace_size()), F.device)
