@@ -10,8 +10,8 @@
 // CTA holds M in shared memory (column j of M is row j of R, contiguous) and
 // runs the l/2 disjoint rotations of a round-robin step in parallel, eight
 // lanes per column pair.  The rotations are logged; a second kernel replays
-// them on the rows of the identity (every row of Z evolves independently) in
-// parallel across CTAs, which keeps Z out of the Jacobi CTA's shared memory.
+// them on the rows of the identity (every row of Z evolves independently, one
+// warp per row), which keeps Z out of the Jacobi CTA's shared memory.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -88,7 +88,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                     mp[e] = cs * x - sn * y;
                     mq[e] = sn * x + cs * y;
                 }
-                if (lane == 0) atomicAdd(&s_rot, 1);
+                s_rot = 1;                       // any rotation this sweep (a flag, not a count)
             }
             if (live && lane == 0)
                 rot[((size_t)sweep * (L - 1) + step) * npairs + g] = make_float2(cs, sn);
@@ -106,7 +106,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
 
     // singular values = column norms; sort descending (ties by index)
     // (warp-uniform trip count: every lane reaches the full-mask shuffles)
-    for (int j0 = 0; j0 < l; j0 += kJacThreads / 8) {
+    for (int j0 = 0; j0 < l; j0 += (int)blockDim.x / 8) {
         const int j = j0 + g;
         float s2 = 0.f;
         if (j < l)
@@ -139,49 +139,55 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
     }
 }
 
-// Z = product of the logged rotations applied to the identity; each CTA owns
-// `rows` rows of Z.  Zk[i][r] = Z[i][perm[r]].
-constexpr int kReplayRows = 2;
+// Z = product of the logged rotations applied to the identity.  Every row of Z
+// evolves independently, so each warp owns one row (in shared memory) and applies
+// the rounds in order, lanes taking the disjoint pairs of a round; the CTA stages
+// the logged rotations through shared memory kReplayChunk rounds at a time.
+// Zk[i][r] = Z[i][perm[r]].
+constexpr int kReplayWarps = 8;
+constexpr int kReplayChunk = 16;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kReplayWarps * 32)
 replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr, int l,
               const int *__restrict__ perm, float *__restrict__ Zk, int lp, int k, int kp) {
-    __shared__ float Z[kReplayRows][RPCA_MAX_L + 1];
+    __shared__ float Z[kReplayWarps][RPCA_MAX_L + 1];
+    __shared__ float2 rs[kReplayChunk][RPCA_MAX_L / 2];
     const int L = even_up(l), npairs = L / 2;
-    const int i0 = blockIdx.x * kReplayRows;
-    for (int e = threadIdx.x; e < kReplayRows * l; e += blockDim.x) {
-        const int rr = e / l, c = e % l;
-        Z[rr][c] = (i0 + rr == c) ? 1.f : 0.f;
-    }
-    __syncthreads();
-    const int sweeps = *sweeps_ptr;
-    const int tasks = kReplayRows * npairs;
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int step = 0; step < L - 1; ++step) {
-            const float2 *rs = rot + ((size_t)sw * (L - 1) + step) * npairs;
-            for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
-                const int rr = t / npairs, g = t % npairs;
-                auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (L - 1); };
-                const int a = player(g), b = player(L - 1 - g);
-                const int p = min(a, b), q = max(a, b);
-                if (q < l) {
-                    const float2 csn = rs[g];
-                    const float x = Z[rr][p], y = Z[rr][q];
-                    Z[rr][p] = csn.x * x - csn.y * y;
-                    Z[rr][q] = csn.y * x + csn.x * y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kReplayWarps + warp;           // this warp's row of Z
+    for (int c = lane; c < l; c += 32) Z[warp][c] = (i == c) ? 1.f : 0.f;
+    const int rounds = *sweeps_ptr * (L - 1);
+    for (int c0 = 0; c0 < rounds; c0 += kReplayChunk) {
+        const int nr = min(kReplayChunk, rounds - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * npairs; e += blockDim.x)
+            rs[e / npairs][e % npairs] = rot[(size_t)c0 * npairs + e];
+        __syncthreads();
+        if (i < l) {
+            for (int r = 0; r < nr; ++r) {
+                const int step = (c0 + r) % (L - 1);
+                for (int g = lane; g < npairs; g += 32) {
+                    const int a = g == 0 ? 0 : 1 + (g - 1 + step) % (L - 1);
+                    const int pb = L - 1 - g;
+                    const int b = pb == 0 ? 0 : 1 + (pb - 1 + step) % (L - 1);
+                    const int p = min(a, b), q = max(a, b);
+                    if (q < l) {
+                        const float2 csn = rs[r][g];
+                        const float x = Z[warp][p], y = Z[warp][q];
+                        Z[warp][p] = csn.x * x - csn.y * y;
+                        Z[warp][q] = csn.y * x + csn.x * y;
+                    }
                 }
+                __syncwarp();
             }
-            __syncthreads();
         }
     }
-    for (int e = threadIdx.x; e < kReplayRows * kp; e += blockDim.x) {
-        const int rr = e / kp, r = e % kp;
-        const int i = i0 + rr;
-        if (i >= lp) continue;
-        float v = 0.f;
-        if (i < l && r < k) v = Z[rr][perm[r]];
-        Zk[(size_t)i * kp + r] = v;
-    }
+    if (i < lp)
+        for (int r = lane; r < kp; r += 32) {
+            float v = 0.f;
+            if (i < l && r < k) v = Z[warp][perm[r]];
+            Zk[(size_t)i * kp + r] = v;
+        }
 }
 
 // Per column r < k: flip V[:, r] when its largest-|entry| (first on ties) is
@@ -234,12 +240,14 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
     const size_t smem = (size_t)l * (l + 1) * sizeof(float);
     cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) * sizeof(float)));
-    jacobi_kernel<<<1, kJacThreads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig,
-                                               perm, Wk, lp, k, kp, st);
+    // eight lanes per column pair of a round; no idle warps at the round barriers
+    const int threads = (int)std::min<int64_t>(kJacThreads, std::max<int64_t>(64, round_up(8 * (even_up(l) / 2), 32)));
+    jacobi_kernel<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig,
+                                           perm, Wk, lp, k, kp, st);
     RPCA_CHECK_LAUNCH();
-    const int grid = (int)cdiv(lp, kReplayRows);
-    replay_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk, lp,
-                                       k, kp);
+    const int grid = (int)cdiv(lp, kReplayWarps);
+    replay_kernel<<<grid, kReplayWarps * 32, 0, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
+                                                     lp, k, kp);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
