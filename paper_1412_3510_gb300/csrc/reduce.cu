@@ -80,27 +80,44 @@ center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
     }
 }
 
-// G[a][b] = sum_s part[s][a][b] (a, b < l), compensated (Kahan) FP32 sum: the
-// result carries FP32-level relative error, as the FP32 Cholesky needs; GB300's
-// FP64 adds run at 1/64 of the FP32 rate.
+// G[a][b] = sum_s part[s][a][b] (a, b < l), compensated (Kahan) FP32 sums in a
+// fixed order: the result carries FP32-level relative error, as the FP32 Cholesky
+// needs (GB300's FP64 adds run at 1/64 of the FP32 rate).  A CTA takes 32
+// consecutive entries of G (threadIdx.x) and eight interleaved groups of the splits
+// (threadIdx.y): every load is a coalesced 128-byte row of a partial, eight
+// independent chains per entry; the eight group sums are combined in order.
 __global__ void __launch_bounds__(256)
 gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G,
                    const int *__restrict__ skip_flag) {
     if (skip_flag && *skip_flag == 0) return;
+    __shared__ float sh[8][32], ch[8][32];
     const int64_t total = (int64_t)l * l;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int y = threadIdx.y;
+    float s = 0.f, comp = 0.f;
+    if (e < total) {
         const int a = (int)(e / l), b = (int)(e % l);
-        float s = 0.f, comp = 0.f;
         const float *p = part + (int64_t)a * lp + b;
         const int64_t stride = (int64_t)lp * lp;
-        for (int q = 0; q < splits; ++q) {
-            const float y = p[q * stride] - comp;
-            const float t = s + y;
-            comp = (t - s) - y;
+        for (int q = y; q < splits; q += 8) {
+            const float v = p[q * stride] - comp;
+            const float t = s + v;
+            comp = (t - s) - v;
             s = t;
         }
-        G[e] = (double)s;
+    }
+    sh[y][threadIdx.x] = s;
+    ch[y][threadIdx.x] = comp;
+    __syncthreads();
+    if (y == 0 && e < total) {
+        float t = 0.f, c = 0.f;
+        for (int g = 0; g < 8; ++g) {
+            const float v = (sh[g][threadIdx.x] - ch[g][threadIdx.x]) - c;
+            const float u = t + v;
+            c = (u - t) - v;
+            t = u;
+        }
+        G[e] = (double)t;
     }
 }
 
@@ -188,8 +205,8 @@ int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, 
 
 int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s,
                        const int *skip_flag) {
-    const int64_t grid = std::min<int64_t>(cdiv((int64_t)l * l, 256), (int64_t)num_sms() * 2);
-    gram_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(part, splits, l, lp, G, skip_flag);
+    gram_reduce_kernel<<<(unsigned)cdiv((int64_t)l * l, (int64_t)32), dim3(32, 8), 0, s>>>(part, splits, l, lp, G,
+                                                                                         skip_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

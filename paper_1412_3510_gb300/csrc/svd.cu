@@ -8,7 +8,7 @@
 // The l x l SVD is one-sided Jacobi (Hestenes; Demmel & Veselic 1992): plane
 // rotations applied on the right orthogonalise the columns of M = R^T.  One
 // CTA holds M in shared memory (column j of M is row j of R, contiguous) and
-// runs the l/2 disjoint rotations of a round-robin step in parallel, eight
+// runs the l/2 disjoint rotations of a round-robin step in parallel, four
 // lanes per column pair.  The rotations are logged; a second kernel replays
 // them on the rows of the identity (every row of Z evolves independently, one
 // warp per row), which keeps Z out of the Jacobi CTA's shared memory.
@@ -21,57 +21,59 @@ namespace rpca {
 namespace {
 
 constexpr int kJacThreads = 1024;
+constexpr int kLanesPerPair = 4;      // lanes sharing one column pair of a round
 constexpr int kMaxSweeps = 40;
 
 __host__ __device__ __forceinline__ int even_up(int l) { return l + (l & 1); }
-
-// Circle-method round robin over L = even_up(l) players: player 0 fixed,
-// the others rotate; pair g of step r.
-__device__ __forceinline__ void rr_pair(int L, int r, int g, int &p, int &q) {
-    auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (L - 1); };
-    const int a = player(g), b = player(L - 1 - g);
-    p = min(a, b);
-    q = max(a, b);
-}
+// row length of the Jacobi CTA's copy of M (16-byte rows for float4 access)
+__host__ __device__ __forceinline__ int jac_ldm(int l) { return (l + 3) & ~3; }
 
 __global__ void __launch_bounds__(kJacThreads)
 jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int *__restrict__ sweeps_out,
               float *__restrict__ sig, int *__restrict__ perm, float *__restrict__ Wk, int lp, int k,
               int kp, DevStatus *__restrict__ st) {
-    extern __shared__ float Ms[];      // l rows of length ldm: row j = column j of M = R^T
-    const int ldm = l + 1;
+    extern __shared__ float4 Ms4[];    // l rows of ldm floats: row j = column j of M = R^T
+    float *Ms = reinterpret_cast<float *>(Ms4);
+    const int ldm = jac_ldm(l);        // multiple of 4, columns l..ldm-1 zero
+    const int nv = ldm / 4;            // float4 per row
     __shared__ int s_rot;
     __shared__ float s_sig[RPCA_MAX_L];
     const int tid = threadIdx.x;
     const int L = even_up(l);
     const int npairs = L / 2;
 
-    for (int e = tid; e < l * l; e += blockDim.x) Ms[(e / l) * ldm + (e % l)] = R[e];
+    for (int e = tid; e < l * ldm; e += blockDim.x) {
+        const int j = e / ldm, c = e - j * ldm;
+        Ms[e] = c < l ? R[(size_t)j * l + c] : 0.f;
+    }
     __syncthreads();
 
-    const int g = tid >> 3, lane = tid & 7;
+    const int g = tid / kLanesPerPair, lane = tid % kLanesPerPair;
+    const bool live = g < npairs;
     const float tol = 8.0f * sqrtf((float)l) * 0x1p-24f;
+    float2 *rlog = rot + g;
     int sweep = 0;
     for (; sweep < kMaxSweeps; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
+        // circle-method round robin: positions g and L-1-g; each step moves every
+        // player but 0 one place along 1..L-1
+        int pa = g == 0 ? 0 : g, pb = L - 1 - g;
         for (int step = 0; step < L - 1; ++step) {
-            int p = 0, q = 0;
-            const bool live = g < npairs;
-            if (live) rr_pair(L, step, g, p, q);
+            const int p = live ? min(pa, pb) : 0, q = live ? max(pa, pb) : 0;
             const bool valid = live && q < l;
             float a = 0.f, b = 0.f, c = 0.f;
+            float4 *mp = Ms4 + p * nv, *mq = Ms4 + q * nv;
             if (valid) {
-                const float *mp = Ms + p * ldm, *mq = Ms + q * ldm;
-                for (int e = lane; e < l; e += 8) {
-                    const float x = mp[e], y = mq[e];
-                    a = fmaf(x, x, a);
-                    b = fmaf(y, y, b);
-                    c = fmaf(x, y, c);
+                for (int e = lane; e < nv; e += kLanesPerPair) {
+                    const float4 x = mp[e], y = mq[e];
+                    a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
+                    b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
+                    c = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, c))));
                 }
             }
 #pragma unroll
-            for (int off = 1; off < 8; off <<= 1) {
+            for (int off = 1; off < kLanesPerPair; off <<= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, off);
                 b += __shfl_xor_sync(0xffffffffu, b, off);
                 c += __shfl_xor_sync(0xffffffffu, c, off);
@@ -82,16 +84,19 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                 const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(zeta, 1.f));
                 cs = rsqrtf(fmaf(t, t, 1.f));
                 sn = cs * t;
-                float *mp = Ms + p * ldm, *mq = Ms + q * ldm;
-                for (int e = lane; e < l; e += 8) {
-                    const float x = mp[e], y = mq[e];
-                    mp[e] = cs * x - sn * y;
-                    mq[e] = sn * x + cs * y;
+                for (int e = lane; e < nv; e += kLanesPerPair) {
+                    const float4 x = mp[e], y = mq[e];
+                    mp[e] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
+                                        cs * x.w - sn * y.w);
+                    mq[e] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
+                                        sn * x.w + cs * y.w);
                 }
                 s_rot = 1;                       // any rotation this sweep (a flag, not a count)
             }
-            if (live && lane == 0)
-                rot[((size_t)sweep * (L - 1) + step) * npairs + g] = make_float2(cs, sn);
+            if (live && lane == 0) *rlog = make_float2(cs, sn);
+            rlog += npairs;
+            pa = pa == 0 ? 0 : (pa == L - 1 ? 1 : pa + 1);
+            pb = pb == 0 ? 0 : (pb == L - 1 ? 1 : pb + 1);
             __syncthreads();
         }
         if (s_rot == 0) { ++sweep; break; }
@@ -106,12 +111,12 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
 
     // singular values = column norms; sort descending (ties by index)
     // (warp-uniform trip count: every lane reaches the full-mask shuffles)
-    for (int j0 = 0; j0 < l; j0 += (int)blockDim.x / 8) {
+    for (int j0 = 0; j0 < l; j0 += (int)blockDim.x / kLanesPerPair) {
         const int j = j0 + g;
         float s2 = 0.f;
         if (j < l)
-            for (int e = lane; e < l; e += 8) s2 = fmaf(Ms[j * ldm + e], Ms[j * ldm + e], s2);
-        for (int off = 1; off < 8; off <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            for (int e = lane; e < l; e += kLanesPerPair) s2 = fmaf(Ms[j * ldm + e], Ms[j * ldm + e], s2);
+        for (int off = 1; off < kLanesPerPair; off <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
         if (j < l && lane == 0) s_sig[j] = sqrtf(s2);
     }
     __syncthreads();
@@ -146,6 +151,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
 // Zk[i][r] = Z[i][perm[r]].
 constexpr int kReplayWarps = 8;
 constexpr int kReplayChunk = 16;
+constexpr int kReplayGroups = (RPCA_MAX_L / 2 + 31) / 32;   // pair groups per lane
 
 __global__ void __launch_bounds__(kReplayWarps * 32)
 replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr, int l,
@@ -157,6 +163,9 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
     const int i = blockIdx.x * kReplayWarps + warp;           // this warp's row of Z
     for (int c = lane; c < l; c += 32) Z[warp][c] = (i == c) ? 1.f : 0.f;
     const int rounds = *sweeps_ptr * (L - 1);
+    // positions of this lane's pair groups g = lane + 32 u in the round-robin circle
+    int pa[kReplayGroups], pb[kReplayGroups];
+    int step = 0;
     for (int c0 = 0; c0 < rounds; c0 += kReplayChunk) {
         const int nr = min(kReplayChunk, rounds - c0);
         __syncthreads();
@@ -164,19 +173,28 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
             rs[e / npairs][e % npairs] = rot[(size_t)c0 * npairs + e];
         __syncthreads();
         if (i < l) {
-            for (int r = 0; r < nr; ++r) {
-                const int step = (c0 + r) % (L - 1);
-                for (int g = lane; g < npairs; g += 32) {
-                    const int a = g == 0 ? 0 : 1 + (g - 1 + step) % (L - 1);
-                    const int pb = L - 1 - g;
-                    const int b = pb == 0 ? 0 : 1 + (pb - 1 + step) % (L - 1);
-                    const int p = min(a, b), q = max(a, b);
-                    if (q < l) {
+            for (int r = 0; r < nr; ++r, ++step) {
+                if (step == L - 1) step = 0;
+                if (step == 0) {                      // a new sweep: the circle starts over
+#pragma unroll
+                    for (int u = 0; u < kReplayGroups; ++u) {
+                        const int g = lane + 32 * u;
+                        pa[u] = g == 0 ? 0 : g;
+                        pb[u] = L - 1 - g;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kReplayGroups; ++u) {
+                    const int g = lane + 32 * u;
+                    const int p = min(pa[u], pb[u]), q = max(pa[u], pb[u]);
+                    if (g < npairs && q < l) {
                         const float2 csn = rs[r][g];
                         const float x = Z[warp][p], y = Z[warp][q];
                         Z[warp][p] = csn.x * x - csn.y * y;
                         Z[warp][q] = csn.y * x + csn.x * y;
                     }
+                    pa[u] = pa[u] == 0 ? 0 : (pa[u] == L - 1 ? 1 : pa[u] + 1);
+                    pb[u] = pb[u] == 0 ? 0 : (pb[u] == L - 1 ? 1 : pb[u] + 1);
                 }
                 __syncwarp();
             }
@@ -237,11 +255,12 @@ size_t small_svd_rot_floats(int l) {
 int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, float *Zk, float *sig,
                      float *rot, float *zbuf, int *perm, DevStatus *st, cudaStream_t s) {
     int *sweeps = reinterpret_cast<int *>(zbuf);
-    const size_t smem = (size_t)l * (l + 1) * sizeof(float);
+    const size_t smem = (size_t)l * jac_ldm(l) * sizeof(float);
     cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) * sizeof(float)));
-    // eight lanes per column pair of a round; no idle warps at the round barriers
-    const int threads = (int)std::min<int64_t>(kJacThreads, std::max<int64_t>(64, round_up(8 * (even_up(l) / 2), 32)));
+                         (int)((size_t)RPCA_MAX_L * jac_ldm(RPCA_MAX_L) * sizeof(float)));
+    // kLanesPerPair lanes per column pair of a round; no idle warps at the round barriers
+    const int threads = (int)std::min<int64_t>(
+        kJacThreads, std::max<int64_t>(64, round_up(kLanesPerPair * (even_up(l) / 2), 32)));
     jacobi_kernel<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig,
                                            perm, Wk, lp, k, kp, st);
     RPCA_CHECK_LAUNCH();
