@@ -36,6 +36,12 @@ namespace {
 using namespace ptx;
 
 constexpr int kBM = 128;              // MMA M and CTA output rows
+// The tensor cores' FP32 accumulation does not round to nearest: the sums drift
+// toward zero by about 2^-27 per accumulated K element (measured: -1.5e-4 relative
+// after K = 20000, -1.6e-3 after K = 200000).  Each TMEM accumulation chain
+// therefore covers at most kChunkRows of K; the epilogue adds the chunks of a tile
+// in FP32 with round-to-nearest, which bounds the drift near 1.5e-5.
+constexpr int kChunkRows = 2048;
 constexpr int kStagesA = 3;           // FP32 A ring depth
 constexpr int kBufs = 2;              // converted BF16 buffers
 
@@ -69,6 +75,7 @@ struct TcArgs {
     int row_tiles;                // 128-row output tiles
     int ntiles;                   // row_tiles x splits
     DevStatus *st;
+    int chunk_st;                 // K stages per TMEM accumulation chain
 };
 
 constexpr int kThreads = 512;     // 16 warps
@@ -181,15 +188,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             const uint32_t idesc = instr_desc_bf16(kBM, N);
             constexpr uint32_t LBO = 128, SBO = (BK / 8) * 128;
             uint32_t g = 0, i = 0;
-            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++i) {
+            for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
                 int64_t row0, kbeg;
                 int nst;
                 tile_info(t, row0, kbeg, nst);
+                const int nch = nst > 0 ? (nst + args.chunk_st - 1) / args.chunk_st : 1;
+                int k = 0;
+                for (int ch = 0; ch < nch && ok; ++ch, ++i) {
                 const uint32_t acc = i & 1;
                 if (i >= 2 && !mbar_wait(&tm_empty[acc], ((i >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
                 tc_fence_after();
                 const uint32_t d = tmem_base + acc * acc_cols;
-                for (int k = 0; k < nst && ok; ++k, ++g) {
+                const int kend = min(nst, k + args.chunk_st);
+                for (int kc = 0; k < kend && ok; ++k, ++kc, ++g) {
                     const int b = g % kBufs;
                     if (!mbar_wait(&full_c[b], (g / kBufs) & 1, abort_flag)) { fail(); break; }
                     tc_fence_after();
@@ -199,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t o = kk * 256;
-                        const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
+                        const uint32_t acc0 = (kc > 0 || kk > 0) ? 1u : 0u;
                         umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, acc0);
                         umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), idesc, 1u);
                         umma_bf16(d, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, 1u);
@@ -207,16 +218,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                     umma_commit(&empty_c[b]);
                 }
                 if (ok) umma_commit(&tm_full[acc]);
+                }
             }
         }
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
         // ---------------- epilogue: TMEM lanes 32*(warp%4)..+31 ----------------
         const int q = warp & 3;
         uint32_t i = 0;
-        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++i) {
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
             int64_t row0, kbeg;
             int nst;
             tile_info(t, row0, kbeg, nst);
+            const int nch = nst > 0 ? (nst + args.chunk_st - 1) / args.chunk_st : 1;
+            for (int ch = 0; ch < nch && ok; ++ch, ++i) {
             const uint32_t acc = i & 1;
             if (!mbar_wait(&tm_full[acc], (i >> 1) & 1, abort_flag)) { fail(); break; }
             tc_fence_after();
@@ -235,20 +249,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                     for (int e = 0; e < 16; ++e) v[e] = 0.f;
                 }
                 if (live) {
+                    // chunk 0 stores; later chunks of the tile add in FP32 (round to nearest)
                     if (vec && c0 + 16 <= args.ncols_store) {
 #pragma unroll
-                        for (int e = 0; e < 16; e += 4)
-                            *reinterpret_cast<float4 *>(orow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                        for (int e = 0; e < 16; e += 4) {
+                            float4 *p4 = reinterpret_cast<float4 *>(orow + c0 + e);
+                            float4 o = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                            if (ch > 0) {
+                                const float4 w = *p4;
+                                o.x += w.x; o.y += w.y; o.z += w.z; o.w += w.w;
+                            }
+                            *p4 = o;
+                        }
                     } else {
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
-                            if (c0 + e < args.ncols_store) orow[c0 + e] = v[e];
+                            if (c0 + e < args.ncols_store) orow[c0 + e] = ch > 0 ? orow[c0 + e] + v[e] : v[e];
                     }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tm_empty[acc]);
+            }
         }
     } else if (warp >= 16 - kConvWarps) {
         // ---------------- converters ----------------
@@ -416,10 +439,21 @@ size_t tc_split_bytes(int64_t rows, int lp) {
 }
 
 int tc_adjoint_splits(int64_t n, int64_t m, int lp) {
-    // enough (column tile, split) work items to give every SM about one
+    // (column tile, split) work items: with fewer tiles than SMs, about one item per
+    // SM; with more, the fewest splits (<= 16) whose items fill >= 90% of the waves
+    // of one CTA per SM (157 tiles on 152 SMs would otherwise take two waves)
     const int64_t tiles = cdiv(n, kBM);
     const int64_t stages = cdiv(m, tc_bk(lp));
-    int64_t s = std::max<int64_t>(1, num_sms() / tiles);
+    const int64_t sms = num_sms();
+    int64_t s = 1;
+    if (tiles <= sms) {
+        s = std::max<int64_t>(1, sms / tiles);
+    } else {
+        for (s = 1; s < 16; ++s) {
+            const int64_t items = tiles * s;
+            if ((double)items / (double)(cdiv(items, sms) * sms) >= 0.9) break;
+        }
+    }
     return (int)std::min<int64_t>(s, std::max<int64_t>(1, stages / 4));
 }
 
@@ -442,7 +476,7 @@ int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __n
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
     const int tiles = (int)cdiv(m, kBM);
-    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st};
+    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK)};
     dim3 grid((unsigned)std::min(tiles, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
 }
@@ -454,7 +488,7 @@ int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const _
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, (uint32_t)BK));
     const int64_t per = round_up(cdiv(m, splits), BK);
     const int rt = (int)cdiv(n, kBM);
-    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st};
+    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st, std::max(1, kChunkRows / BK)};
     dim3 grid((unsigned)std::min(rt * splits, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
 }

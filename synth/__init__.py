@@ -113,13 +113,15 @@ def haar_dense_np(m: int, n: int, sigma: np.ndarray, seed: int, dtype=np.float32
     return ((u * np.asarray(sigma[:r])[None, :]) @ v.T).astype(dtype)
 
 
-def haar_dense_torch(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda"):
+def haar_dense_torch(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda", return_colsum: bool = False):
     """Same construction on a torch device (for matrices too large for the host).
 
     The QR runs in FP32 on the device; the singular values of the stored FP32
     matrix therefore differ from ``sigma`` at the 1e-6 relative level, which is
-    why exact reference singular values are always recomputed from the stored
-    matrix rather than taken from ``sigma``.
+    why exact reference singular values are recomputed from the stored matrix
+    where that is affordable.  return_colsum: also return U^T 1 (FP64 host
+    vector of length min(m, n), U the FP32 orthonormal factor used), the input
+    metadata from which the spectrum of the column-centred matrix follows.
     """
     import torch
     r = min(m, n)
@@ -134,11 +136,17 @@ def haar_dense_torch(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda"
         return q
 
     u = haar(m, r)
+    colsum = None
+    if return_colsum:
+        cs = torch.zeros(r, dtype=torch.float64, device=device)
+        for i in range(0, m, 8192):
+            cs += u[i:i + 8192].double().sum(0)
+        colsum = cs.cpu().numpy()
     u.mul_(torch.as_tensor(np.asarray(sigma[:r]), dtype=torch.float32, device=device)[None, :])
     v = haar(n, r)
     a = u @ v.T
     del u, v
-    return a.contiguous()
+    return (a.contiguous(), colsum) if return_colsum else a.contiguous()
 
 
 def e2_matrix_np(n: int, seed: int) -> np.ndarray:

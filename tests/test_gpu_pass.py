@@ -67,3 +67,22 @@ def test_bf16x3_special_values():
     B = np.arange(192 * 16, dtype=np.float32).reshape(192, 16) % 7 - 3
     C = to_np(rp.rpca_dense_pass(to_dev(A), to_dev(B), precision="bf16x3"))
     assert np.array_equal(C, (A.astype(np.float64) @ B.astype(np.float64)))
+
+
+@pytest.mark.parametrize("m,n,w,adjoint", [(4096, 20000, 224, False), (120000, 4096, 224, True)])
+def test_bf16x3_long_accumulation_has_no_drift(m, n, w, adjoint):
+    """All-positive operands make any one-signed accumulation error visible: the
+    split-BF16 products over long K must stay unbiased against FP64 (the tensor
+    cores' FP32 accumulation drifts toward zero on long chains)."""
+    torch = cuda()
+    import paper_1412_3510_gb300 as rp
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    A = torch.rand(m, n, device="cuda", generator=g)
+    B = torch.rand(m if adjoint else n, w, device="cuda", generator=g)
+    C = rp.rpca_dense_pass(A, B, adjoint=adjoint, precision="bf16x3")
+    rows = torch.arange(0, C.shape[0], C.shape[0] // 16, device="cuda")[:16]
+    ref = (A[:, rows].double().T if adjoint else A[rows].double()) @ B.double()
+    rel = ((C[rows].double() - ref) / ref).cpu().numpy()
+    assert abs(rel.mean()) < 3e-5, rel.mean()
+    assert np.abs(rel).max() < 1e-4, np.abs(rel).max()
