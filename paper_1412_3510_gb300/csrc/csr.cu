@@ -4,9 +4,9 @@
 // call by a stable radix sort of the nonzeros by column (no atomics anywhere,
 // so every result is deterministic).
 //
-// SpMM: one warp per row, lanes across the l-wide block (the block operand is
-// read from L2 row by row), eight nonzeros per step so that eight gathers are
-// in flight per warp.  Rows with more than kHeavy nonzeros (power-law degree
+// SpMM: a group of 8, 16 or 32 lanes per row (by the block width), lanes across
+// the l-wide block in float4 (the block operand is read from L2 row by row), four
+// nonzeros per step, several rows per warp so that many gathers are in flight.  Rows with more than kHeavy nonzeros (power-law degree
 // distributions have rows with ~1e5 of them) are cut into chunks of kHeavy
 // nonzeros, one warp per chunk writing a partial row, and a third kernel adds
 // each heavy row's partials in chunk order.
@@ -58,22 +58,89 @@ radix_hist_kernel(const int32_t *__restrict__ keys, int64_t count, int shift, in
     for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[(int64_t)b * nblocks + blockIdx.x] = h[b];
 }
 
-// in-place exclusive scan of `total` counts, one CTA
-__global__ void __launch_bounds__(1024) scan_kernel(int32_t *__restrict__ data, int64_t total) {
-    __shared__ int64_t sums[1024];
-    const int64_t per = (total + blockDim.x - 1) / blockDim.x;
-    const int64_t b = threadIdx.x * per, e = min(total, b + per);
+// In-place exclusive scan of `total` counts in three launches: per-tile sums, a
+// scan of the tile sums (one CTA), and per-tile scans with the tile offsets.
+constexpr int kScanThreads = 256, kScanPer = 16, kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(const int32_t *__restrict__ data, int64_t total,
+                                                                 int64_t *__restrict__ sums) {
+    __shared__ int64_t red[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += data[i];
-    sums[threadIdx.x] = s;
+    for (int e = threadIdx.x; e < kScanTile; e += kScanThreads) {
+        const int64_t i = base + e;
+        if (i < total) s += data[i];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) scan_top_kernel(int64_t *__restrict__ sums, int64_t n) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(n, b + per);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += sums[i];
+    part[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int64_t run = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) { const int64_t v = sums[t]; sums[t] = run; run += v; }
+        for (int t = 0; t < (int)blockDim.x; ++t) { const int64_t v = part[t]; part[t] = run; run += v; }
     }
     __syncthreads();
-    int64_t run = sums[threadIdx.x];
-    for (int64_t i = b; i < e; ++i) { const int32_t v = data[i]; data[i] = (int32_t)run; run += v; }
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) { const int64_t v = sums[i]; sums[i] = run; run += v; }
+}
+
+// thread t scans kScanPer consecutive entries of the tile
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(int32_t *__restrict__ data, int64_t total,
+                                                                  const int64_t *__restrict__ sums) {
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int32_t v[kScanPer];
+    int64_t own = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+        v[u] = base + u < total ? data[base + u] : 0;
+        own += v[u];
+    }
+    int64_t incl = own;                               // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int64_t before = sums[blockIdx.x] + incl - own;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+#pragma unroll
+    for (int u = 0; u < kScanPer; ++u) {
+        if (base + u < total) data[base + u] = (int32_t)before;
+        before += v[u];
+    }
+}
+
+int64_t scan_tiles(int64_t total) { return std::max<int64_t>(1, cdiv(total, (int64_t)kScanTile)); }
+
+int launch_scan(int32_t *data, int64_t total, int64_t *sums, cudaStream_t s) {
+    if (total <= 0) return RPCA_OK;
+    const int64_t tiles = scan_tiles(total);
+    scan_sums_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, total, sums);
+    RPCA_CHECK_LAUNCH();
+    scan_top_kernel<<<1, 1024, 0, s>>>(sums, tiles);
+    RPCA_CHECK_LAUNCH();
+    scan_apply_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, total, sums);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
 }
 
 // stable scatter by digit: warp w of a block handles nonzeros [block*kTile + 512 w, +512) in order
@@ -224,6 +291,122 @@ spmm_light_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ i
     }
 }
 
+// a0, a1 (two float4 of a G-lane group's share of the l-wide row: columns 4 sub and
+// 4 (sub + G)) += sum_{p0 <= p < p1} val[p] X[idx[p]], four nonzeros per step;
+// entries with a column outside [0, cols) contribute nothing.
+template <int G>
+__device__ __forceinline__ void group_dot(const int32_t *__restrict__ idx, const float *__restrict__ val, int32_t p0,
+                                          int32_t p1, int64_t cols, const float4 *__restrict__ X4, int nv, int sub,
+                                          bool c0ok, bool c1ok, float4 &a0, float4 &a1) {
+    int32_t p = p0;
+    for (; p + 4 <= p1; p += 4) {
+        int32_t j[4];
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = __ldg(idx + p + u);
+            v[u] = __ldg(val + p + u);
+            if ((uint32_t)j[u] >= (uint32_t)cols) { j[u] = 0; v[u] = 0.f; }
+        }
+        float4 x0[4], x1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 *xr = X4 + (int64_t)j[u] * nv;
+            x0[u] = c0ok ? __ldg(xr + sub) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x1[u] = c1ok ? __ldg(xr + sub + G) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a0.x = fmaf(v[u], x0[u].x, a0.x); a0.y = fmaf(v[u], x0[u].y, a0.y);
+            a0.z = fmaf(v[u], x0[u].z, a0.z); a0.w = fmaf(v[u], x0[u].w, a0.w);
+            a1.x = fmaf(v[u], x1[u].x, a1.x); a1.y = fmaf(v[u], x1[u].y, a1.y);
+            a1.z = fmaf(v[u], x1[u].z, a1.z); a1.w = fmaf(v[u], x1[u].w, a1.w);
+        }
+    }
+    for (; p < p1; ++p) {
+        const int32_t jj = __ldg(idx + p);
+        if ((uint32_t)jj >= (uint32_t)cols) continue;
+        const float vv = __ldg(val + p);
+        const float4 *xr = X4 + (int64_t)jj * nv;
+        if (c0ok) {
+            const float4 x = __ldg(xr + sub);
+            a0.x = fmaf(vv, x.x, a0.x); a0.y = fmaf(vv, x.y, a0.y); a0.z = fmaf(vv, x.z, a0.z); a0.w = fmaf(vv, x.w, a0.w);
+        }
+        if (c1ok) {
+            const float4 x = __ldg(xr + sub + G);
+            a1.x = fmaf(vv, x.x, a1.x); a1.y = fmaf(vv, x.y, a1.y); a1.z = fmaf(vv, x.z, a1.z); a1.w = fmaf(vv, x.w, a1.w);
+        }
+    }
+}
+
+// light rows with several rows per warp: a group of G lanes per row, every warp keeping
+// (32 / G) x 4 x 2 float4 gathers in flight.  Needs lp % 4 == 0 and lp <= 8 G; heavy
+// rows are skipped.
+template <int G>
+__global__ void __launch_bounds__(256, 4)
+spmm_light_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                        const float *__restrict__ val, int64_t rows, int64_t cols, int64_t nnz,
+                        const float *__restrict__ X, int lp, float *__restrict__ Y) {
+    constexpr int R = 32 / G;                  // rows per warp
+    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nv = lp >> 2;
+    const bool c0ok = sub < nv, c1ok = sub + G < nv;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    for (int64_t rb = wid * R; rb < rows; rb += nw * R) {
+        const int64_t r = rb + grp;
+        int32_t p0 = 0, p1 = 0;
+        bool write = false;
+        if (r < rows) {
+            p0 = max(ptr[r], 0);
+            p1 = (int32_t)min((int64_t)ptr[r + 1], nnz);
+            write = p1 - p0 <= kHeavy;
+            if (!write) p1 = p0;
+        }
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        group_dot<G>(idx, val, p0, p1, cols, X4, nv, sub, c0ok, c1ok, a0, a1);
+        if (write) {
+            float4 *yr = reinterpret_cast<float4 *>(Y) + r * nv;
+            if (c0ok) yr[sub] = a0;
+            if (c1ok) yr[sub + G] = a1;
+        }
+    }
+}
+
+// heavy chunks, a G-lane group per chunk: part[chunk] = sum over the chunk's nonzeros
+template <int G>
+__global__ void __launch_bounds__(256, 4)
+spmm_heavy_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                        const float *__restrict__ val, const int32_t *__restrict__ first, int64_t rows,
+                        int64_t cols, int64_t nnz, const int2 *__restrict__ table, int64_t max_chunks,
+                        const float *__restrict__ X, int lp, float *__restrict__ part) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nv = lp >> 2;
+    const bool c0ok = sub < nv, c1ok = sub + G < nv;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    const int64_t nchunks = min((int64_t)first[rows], max_chunks);
+    for (int64_t cb = wid * R; cb < nchunks; cb += nw * R) {
+        const int64_t ch = cb + grp;
+        int32_t p0 = 0, p1 = 0;
+        if (ch < nchunks) {
+            const int2 rq = table[ch];
+            p0 = max(ptr[rq.x] + rq.y * kHeavy, 0);
+            p1 = (int32_t)min(min((int64_t)ptr[rq.x + 1], (int64_t)p0 + kHeavy), nnz);
+        }
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        group_dot<G>(idx, val, p0, p1, cols, X4, nv, sub, c0ok, c1ok, a0, a1);
+        if (ch < nchunks) {
+            float4 *pr = reinterpret_cast<float4 *>(part) + ch * nv;
+            if (c0ok) pr[sub] = a0;
+            if (c1ok) pr[sub + G] = a1;
+        }
+    }
+}
+
 // heavy chunks: part[chunk] = sum over the chunk's nonzeros
 __global__ void __launch_bounds__(256)
 spmm_heavy_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, const float *__restrict__ val,
@@ -250,19 +433,23 @@ spmm_heavy_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ i
     }
 }
 
-// heavy rows: Y[r] = sum of its chunk partials in chunk order
+// heavy rows: Y[r] = sum of its chunk partials in chunk order; one warp per row,
+// found through the chunk table (the row's first chunk, q = 0)
 __global__ void __launch_bounds__(256)
-spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, int64_t rows, int64_t max_chunks,
-                         const float *__restrict__ part, int lp, float *__restrict__ Y) {
+spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, const int2 *__restrict__ table, int64_t rows,
+                         int64_t max_chunks, const float *__restrict__ part, int lp, float *__restrict__ Y) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = wid; r < rows; r += nw) {
+    const int64_t nchunks = min((int64_t)first[rows], max_chunks);
+    for (int64_t ch = wid; ch < nchunks; ch += nw) {
+        const int2 rq = table[ch];
+        if (rq.y != 0) continue;
+        const int64_t r = rq.x;
         const int64_t c0 = first[r], c1 = min((int64_t)first[r + 1], max_chunks);
-        if (c1 <= c0) continue;
         for (int c = lane; c < lp; c += 32) {
             float s = 0.f;
-            for (int64_t ch = c0; ch < c1; ++ch) s += part[ch * lp + c];
+            for (int64_t k = c0; k < c1; ++k) s += part[k * lp + c];
             Y[r * lp + c] = s;
         }
     }
@@ -280,12 +467,12 @@ struct Spmm {
     int32_t *first = nullptr;      // rows + 1
     int2 *table = nullptr;         // max_chunks
     float *part = nullptr;         // max_chunks x max_lp
+    int64_t *scan_tmp = nullptr;   // scan_tiles(rows + 1)
 
     int plan(cudaStream_t s) const {
         chunk_count_kernel<<<grid_for(rows + 1, 256), 256, 0, s>>>(ptr, rows, first);
         RPCA_CHECK_LAUNCH();
-        scan_kernel<<<1, 1024, 0, s>>>(first, rows + 1);
-        RPCA_CHECK_LAUNCH();
+        RPCA_TRY(launch_scan(first, rows + 1, scan_tmp, s));
         if (max_chunks > 0) {
             chunk_table_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ptr, first, rows, table, max_chunks);
             RPCA_CHECK_LAUNCH();
@@ -293,13 +480,35 @@ struct Spmm {
         return RPCA_OK;
     }
     int run(const float *X, int lp, float *Y, cudaStream_t s) const {
-        spmm_light_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+        const bool vec = lp % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
+                         (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
+        if (vec && lp <= 64) {
+            spmm_light_group_kernel<8><<<grid_for(rows * 8, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+        } else if (vec && lp <= 128) {
+            spmm_light_group_kernel<16><<<grid_for(rows * 16, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+        } else if (vec && lp <= 256) {
+            spmm_light_group_kernel<32><<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+        } else {
+            spmm_light_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+        }
         RPCA_CHECK_LAUNCH();
         if (max_chunks > 0) {
-            spmm_heavy_kernel<<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(ptr, idx, val, first, rows, cols, nnz,
-                                                                            table, max_chunks, X, lp, part);
+            if (vec && lp <= 64) {
+                spmm_heavy_group_kernel<8><<<grid_for(max_chunks * 8, 256), 256, 0, s>>>(
+                    ptr, idx, val, first, rows, cols, nnz, table, max_chunks, X, lp, part);
+            } else if (vec && lp <= 128) {
+                spmm_heavy_group_kernel<16><<<grid_for(max_chunks * 16, 256), 256, 0, s>>>(
+                    ptr, idx, val, first, rows, cols, nnz, table, max_chunks, X, lp, part);
+            } else if (vec && lp <= 256) {
+                spmm_heavy_group_kernel<32><<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(
+                    ptr, idx, val, first, rows, cols, nnz, table, max_chunks, X, lp, part);
+            } else {
+                spmm_heavy_kernel<<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(ptr, idx, val, first, rows, cols,
+                                                                                nnz, table, max_chunks, X, lp, part);
+            }
             RPCA_CHECK_LAUNCH();
-            spmm_heavy_reduce_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(first, rows, max_chunks, part, lp, Y);
+            spmm_heavy_reduce_kernel<<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(first, table, rows, max_chunks,
+                                                                                   part, lp, Y);
             RPCA_CHECK_LAUNCH();
         }
         return RPCA_OK;
@@ -314,7 +523,7 @@ int64_t max_chunks_for(int64_t nnz, int64_t rows) {
 
 struct CsrScratch {
     size_t row_of = 0, keys0 = 0, keys1 = 0, rows0 = 0, rows1 = 0, vals0 = 0, vals1 = 0, hist = 0, tptr = 0,
-           first_a = 0, first_t = 0, table_a = 0, table_t = 0, part_a = 0, part_t = 0, total = 0;
+           first_a = 0, first_t = 0, table_a = 0, table_t = 0, part_a = 0, part_t = 0, scan = 0, total = 0;
 };
 
 CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
@@ -337,6 +546,7 @@ CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
     S.table_t = take((size_t)max_chunks_for(nnz, n) * 8);
     S.part_a = take((size_t)max_chunks_for(nnz, m) * max_lp * 4);
     S.part_t = take((size_t)max_chunks_for(nnz, n) * max_lp * 4);
+    S.scan = take((size_t)scan_tiles(std::max({(int64_t)256 * nblocks, m + 1, n + 1})) * 8);
     S.total = off;
     return S;
 }
@@ -358,6 +568,7 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     op.a.ptr = row_ptr; op.a.idx = col_idx; op.a.val = val;
     op.a.rows = m; op.a.cols = n; op.a.nnz = nnz; op.a.max_chunks = max_chunks_for(nnz, m);
     op.a.first = I(S.first_a); op.a.table = reinterpret_cast<int2 *>(base + S.table_a); op.a.part = F(S.part_a);
+    op.a.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
 
     int32_t *keys[2] = {I(S.keys0), I(S.keys1)};
     int32_t *rws[2] = {I(S.rows0), I(S.rows1)};
@@ -378,8 +589,7 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
         for (int shift = 0; shift < bits; shift += 8) {
             radix_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(keys[cur], nnz, shift, I(S.hist), nblocks);
             RPCA_CHECK_LAUNCH();
-            scan_kernel<<<1, 1024, 0, s>>>(I(S.hist), (int64_t)256 * nblocks);
-            RPCA_CHECK_LAUNCH();
+            RPCA_TRY(launch_scan(I(S.hist), (int64_t)256 * nblocks, reinterpret_cast<int64_t *>(base + S.scan), s));
             radix_scatter_kernel<<<nblocks, kSortThreads, 0, s>>>(keys[cur], rws[cur], vls[cur], nnz, shift, I(S.hist),
                                                                  nblocks, keys[cur ^ 1], rws[cur ^ 1], vls[cur ^ 1]);
             RPCA_CHECK_LAUNCH();
@@ -391,6 +601,7 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     op.t.ptr = I(S.tptr); op.t.idx = rws[cur]; op.t.val = vls[cur];
     op.t.rows = n; op.t.cols = m; op.t.nnz = nnz; op.t.max_chunks = max_chunks_for(nnz, n);
     op.t.first = I(S.first_t); op.t.table = reinterpret_cast<int2 *>(base + S.table_t); op.t.part = F(S.part_t);
+    op.t.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
     RPCA_TRY(op.a.plan(s));
     RPCA_TRY(op.t.plan(s));
     return RPCA_OK;
