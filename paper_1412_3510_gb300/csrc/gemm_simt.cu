@@ -241,11 +241,103 @@ int choose_splits(int64_t M, int64_t N, int64_t K) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 4096));
 }
 
+// C (M x N) = A (M x K) B (K x N) for the small right-hand factors of the
+// pipeline (Y R^-1 with K = N = lp, the lifts Q W and Q2 Z with N = k): B whole in
+// shared memory, a 64-row tile of A, a 16 x 16 thread grid where thread (ty, tx)
+// owns rows ty + 16 i (i < 4) and columns tx + 16 j (j < NG).  copy_flag == 0 makes
+// B the identity (C = A, N == K).
+constexpr int kSkRows = 64;
+
+template <int NG>
+__global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int K, const float *__restrict__ A,
+                                                          int64_t lda, const float *__restrict__ B, int64_t ldb,
+                                                          float *__restrict__ C, int64_t ldc,
+                                                          const int *__restrict__ copy_flag) {
+    extern __shared__ float sk[];
+    constexpr int NB = 16 * NG;                  // B columns in shared memory
+    const int lda_s = K + 1;                     // odd: the 16 row-owners hit 16 banks
+    float *Bs = sk;                              // K x NB
+    float *As = sk + (size_t)K * NB;             // kSkRows x lda_s
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * kSkRows;
+    if (copy_flag && *copy_flag == 0) {
+        for (int e = tid; e < kSkRows * N; e += 256) {
+            const int64_t r = m0 + e / N;
+            const int c = e % N;
+            if (r < M) C[r * ldc + c] = A[r * lda + c];
+        }
+        return;
+    }
+    for (int e = tid; e < K * NB; e += 256) {
+        const int k = e / NB, c = e - k * NB;
+        Bs[e] = c < N ? B[(int64_t)k * ldb + c] : 0.f;
+    }
+    for (int e = tid; e < kSkRows * K; e += 256) {
+        const int r = e / K, k = e - r * K;
+        As[r * lda_s + k] = m0 + r < M ? A[(m0 + r) * lda + k] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][NG];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < NG; ++j) acc[i][j] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float a[4], b[NG];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[(ty + 16 * i) * lda_s + k];
+#pragma unroll
+        for (int j = 0; j < NG; ++j) b[j] = Bs[k * NB + tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < NG; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = m0 + ty + 16 * i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < NG; ++j) {
+            const int c = tx + 16 * j;
+            if (c < N) C[r * ldc + c] = acc[i][j];
+        }
+    }
+}
+
+template <int NG>
+int launch_smallk(int64_t M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
+                  int64_t ldc, cudaStream_t s, const int *copy_flag) {
+    const size_t smem = ((size_t)K * 16 * NG + (size_t)kSkRows * (K + 1)) * sizeof(float);
+    if (cudaFuncSetAttribute(smallk_gemm_kernel<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return RPCA_ERR_CUDA;
+    smallk_gemm_kernel<NG><<<(unsigned)cdiv(M, (int64_t)kSkRows), 256, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
+                                                                                   copy_flag);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
 int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                  const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
                  int64_t split_stride, cudaStream_t s, const int *copy_flag) {
     if (M <= 0 || N <= 0) return RPCA_OK;
     if (splits < 1) splits = 1;
+    if (!trans_a && splits == 1 && K >= 1 && K <= 160 && N <= 160 && (!copy_flag || N == K)) {
+        const int ng = (int)cdiv(N, (int64_t)16), n = (int)N, k = (int)K;
+        switch (ng) {
+            case 1: return launch_smallk<1>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 2: return launch_smallk<2>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 3: return launch_smallk<3>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 4: return launch_smallk<4>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 5: return launch_smallk<5>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 6: return launch_smallk<6>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 7: return launch_smallk<7>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 8: return launch_smallk<8>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 9: return launch_smallk<9>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            default: return launch_smallk<10>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+        }
+    }
     if (N <= 16) return launch_cfg<128, 16, 4, 2>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
     if (N <= 32) return launch_cfg<128, 32, 4, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
     if (N <= 64) return launch_cfg<128, 64, 8, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
