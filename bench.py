@@ -301,8 +301,12 @@ def run_batched(args, w, dev, world, rank, barrier):
     stream = torch.cuda.current_stream()
 
     per_graph = {}
+    tuning = {}
 
     def graph_for(its):
+        # autotune the tile shape on this batch (untimed); later calls use the choice
+        rpt, tms = rp.rpca_batched_tune(batch, l, its=its, raw=raw, seed=1 + rank, ws=ws)
+        tuning[str(its)] = {"rows_per_thread": rpt, "ms_for_2_4_8": tms}
         for _ in range(args.warmup):
             rp.rpca_batched(batch, l, its=its, raw=raw, seed=1 + rank, ws=ws, check=False)
         torch.cuda.synchronize()
@@ -412,6 +416,7 @@ def run_batched(args, w, dev, world, rank, barrier):
                    "format": "batched dense", "m_range": list(w["m_range"]), "n_range": list(w["n_range"]),
                    "A_bytes": int(4 * mn), "l2": "batch (%.1f GB) is larger than L2; no flush" % (4 * mn / 1e9),
                    "launch": "one CUDA graph replay per step (check, order, persistent kernel)",
+                   "tile_autotune": tuning,
                    "parallelism": f"replicas x{world}"},
         "gbs_per_pass": achieved, "its_sweep_pca_per_s": {str(kk): v for kk, v in sweep.items()} | {str(its): value},
         "accuracy": {"sample": int(ratios.size), "resid_over_sigma_k1_median": float(np.median(ratios)),

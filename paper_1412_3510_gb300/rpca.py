@@ -352,6 +352,33 @@ def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = F
     return batch.U, batch.S, batch.V
 
 
+def rpca_batched_tune(batch: Batch, l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
+                      col_weights=None, ws: torch.Tensor | None = None, stream=None):
+    """Time the batched kernel's tile shapes on this batch and keep the fastest for later
+    rpca_batched calls on batches of the same shape.  Returns (rows_per_thread, [ms x 3])."""
+    k = batch.k
+    opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr")
+    lib = L.load()
+    count = len(batch.mats)
+    need = int(lib.rpca_batched_workspace_size(count, batch.max_m, batch.max_n, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_batched_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, batch.desc.device)
+    wptr = None
+    if isinstance(col_weights, torch.Tensor):
+        wptr = col_weights
+    elif col_weights is not None:
+        wptr = weights_table(col_weights, batch.desc.device)
+        batch._wkeep = (col_weights, wptr)
+    rpt = C.c_int32(0)
+    ms = (C.c_float * 3)()
+    _check(lib.rpca_batched_tune(count, _ptr(batch.desc), batch.max_m, batch.max_n, C.byref(opts), _ptr(wptr),
+                                 _ptr(batch.status), _ptr(ws), ws.numel(), _stream(stream), C.byref(rpt), ms),
+           "rpca_batched_tune")
+    return int(rpt.value), [float(x) for x in ms]
+
+
 # ---------------------------------------------------------------------------
 # learned sketch weighting
 # ---------------------------------------------------------------------------

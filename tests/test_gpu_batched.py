@@ -83,3 +83,22 @@ def test_batched_column_weights():
         om = O.gaussian_omega(a.shape[1], 7, 2) * w[:, None].astype(np.float64)
         _, so, _ = O.rpca(a, 5, 7, 1, omega=om)
         assert np.allclose(to_np(s), so, rtol=1e-4, atol=1e-6 * so[0])
+
+
+def test_batched_tuner_keeps_results_identical():
+    """The autotuner times the tile shapes on the batch; every shape gives bit-identical
+    outputs (each output sums in the same order), and later calls use the choice."""
+    torch = cuda()
+    import paper_1412_3510_gb300 as rp
+    mats = _batch(40, 7, m_range=(100, 3000), n_range=(30, 600))
+    batch = rp.Batch([to_dev(a) for a in mats], 6)
+    U1, S1, V1 = rp.rpca_batched(batch, 8, its=1, seed=3)
+    ref = [(u.clone(), s.clone(), v.clone()) for u, s, v in zip(U1, S1, V1)]
+    rpt, ms = rp.rpca_batched_tune(batch, 8, its=1, seed=3)
+    assert rpt in (2, 4, 8) and all(t > 0 for t in ms)
+    for (u, s, v), (u0, s0, v0) in zip(zip(batch.U, batch.S, batch.V), ref):    # last tuning run: 8 rows
+        assert torch.equal(u, u0) and torch.equal(s, s0) and torch.equal(v, v0)
+    U3, S3, V3 = rp.rpca_batched(batch, 8, its=1, seed=3)                      # the tuned shape
+    for (u, s, v), (u0, s0, v0) in zip(zip(U3, S3, V3), ref):
+        assert torch.equal(u, u0) and torch.equal(s, s0) and torch.equal(v, v0)
+    assert np.all(batch.status.cpu().numpy() == 0)
