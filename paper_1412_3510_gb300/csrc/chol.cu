@@ -213,9 +213,12 @@ chol_inv_reg_kernel(const double *__restrict__ G, int l, int lp, float *__restri
             const float inv_d = 1.0f / d;
             const float inv_r = rsqrtf(d);
             for (int t = tid; t < l - j; t += nt) R[j * ld + j + t] = t == 0 ? d * inv_r : rb[j + t] * inv_r;
+            // slots run in increasing row order, so the finished ones (row <= j) form a
+            // prefix: walk down from the last slot and stop at the first finished one
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                if (si[s] > j && sk[s] < l) {
+            for (int s = NS - 1; s >= 0; --s) {
+                if (si[s] <= j) break;
+                if (sk[s] < l) {
                     a[s] = fmaf(-(rb[si[s]] * inv_d), rb[sk[s]], a[s]);
                     if (si[s] == j + 1) rn[sk[s]] = a[s];
                 }
