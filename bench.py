@@ -348,8 +348,8 @@ def run_batched(args, w, dev, world, rank, barrier):
 
     def graph_for(its):
         # autotune the tile shape on this batch (untimed); later calls use the choice
-        rpt, tms = rp.rpca_batched_tune(batch, l, its=its, raw=raw, seed=1 + rank, ws=ws)
-        tuning[str(its)] = {"rows_per_thread": rpt, "ms_for_2_4_8": tms}
+        shape, tms = rp.rpca_batched_tune(batch, l, its=its, raw=raw, seed=1 + rank, ws=ws)
+        tuning[str(its)] = {"rows_per_thread": shape[0], "k_depth": shape[1], "ms_2x64_4x32_8x32": tms}
         for _ in range(args.warmup):
             rp.rpca_batched(batch, l, its=its, raw=raw, seed=1 + rank, ws=ws, check=False)
         torch.cuda.synchronize()

@@ -155,16 +155,18 @@ int rpca_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64
                  const float *const *col_weights, int32_t *item_status, void *ws, size_t ws_bytes,
                  rpca_stream_t stream);
 
-/* Autotuner of the batched kernel's tile shape: runs rpca_batched on this batch
- * with 2, 4 and 8 rows (columns) of A per thread in its passes (one warm-up and
- * one timed run each, CUDA events on `stream`; waits for `stream`), and records
- * the fastest for batches of the same (count, max_m, max_n, l, k, its, raw):
- * later rpca_batched calls with that key use it (default: 4).  The outputs are
- * those of a complete rpca_batched run and do not depend on the tile shape.
- * rows_per_thread (may be NULL): the choice; ms (may be NULL): the three times. */
+/* Autotuner of the batched kernel's pass tiles: runs rpca_batched on this batch
+ * with each tile shape (rows or columns of A per thread x K depth: 2 x 64,
+ * 4 x 32, 8 x 32; one warm-up and one timed run each, CUDA events on
+ * `stream`; waits for `stream`), and records the fastest for batches of the
+ * same (count, max_m, max_n, l, k, its, raw): later rpca_batched calls with that
+ * key use it (default: 4 x 32).  The outputs are those of a complete
+ * rpca_batched run and do not depend on the tile shape.  rows_per_thread and
+ * depth (may be NULL): the choice; ms (may be NULL): the three times. */
 int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n,
                       const rpca_opts *o, const float *const *col_weights, int32_t *item_status, void *ws,
-                      size_t ws_bytes, rpca_stream_t stream, int32_t *rows_per_thread, float *ms);
+                      size_t ws_bytes, rpca_stream_t stream, int32_t *rows_per_thread, int32_t *depth,
+                      float *ms);
 
 /* ------------------------------------------------------------------------
  * Spectral-norm residual estimate ||A_c - U diag(S) V^T||_2 by the power

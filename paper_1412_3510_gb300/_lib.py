@@ -56,7 +56,7 @@ SIGNATURES = [
     ("rpca_batched_workspace_size", _SZ, [_I32, _I64, _I64, _OPTS]),
     ("rpca_batched", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P]),
     ("rpca_batched_tune", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P, C.POINTER(C.c_int32),
-                                    C.POINTER(C.c_float)]),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     ("rpca_features_workspace_size", _SZ, [_I64, _I64]),
     ("rpca_sketch_features", C.c_int, [_P, _I64, _I64, _I64, _I32, _U64, _P, _P, _SZ, _P]),
     ("rpca_batched_features_workspace_size", _SZ, [_I64]),

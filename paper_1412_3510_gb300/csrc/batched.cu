@@ -84,11 +84,15 @@ extern "C" size_t rpca_batched_workspace_size(int32_t count, int64_t max_m, int6
 
 namespace {
 
-// Tuned tile shapes (rows of A per thread in the passes), keyed by the batch's shape
-// and the method's parameters; filled by rpca_batched_tune.
+// Tuned pass-tile shapes (index into kShapes), keyed by the batch's shape and the
+// method's parameters; filled by rpca_batched_tune.
 using TuneKey = std::tuple<int32_t, int64_t, int64_t, int32_t, int32_t, int32_t, int32_t>;
 std::mutex g_tune_mutex;
 std::map<TuneKey, int> g_tuned;
+struct Shape { int rows, depth; };
+constexpr int kNumShapes = 3;
+constexpr Shape kShapes[kNumShapes] = {{2, 64}, {4, 32}, {8, 32}};
+constexpr int kDefaultShape = 1;             // 4 rows, 32 deep
 
 TuneKey tune_key(int32_t count, int64_t max_m, int64_t max_n, const rpca_opts *o) {
     return TuneKey(count, max_m, max_n, o->l, o->k, o->its, o->raw ? 1 : 0);
@@ -97,7 +101,7 @@ TuneKey tune_key(int32_t count, int64_t max_m, int64_t max_n, const rpca_opts *o
 int tuned_rpt(const TuneKey &key) {
     std::lock_guard<std::mutex> g(g_tune_mutex);
     const auto it = g_tuned.find(key);
-    return it == g_tuned.end() ? 4 : it->second;
+    return it == g_tuned.end() ? kDefaultShape : it->second;
 }
 
 int check_args(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n, const rpca_opts *o,
@@ -112,7 +116,7 @@ int check_args(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t
 }
 
 int run_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, const rpca_opts *o,
-                const float *const *col_weights, int32_t *item_status, void *ws, cudaStream_t s, int rpt) {
+                const float *const *col_weights, int32_t *item_status, void *ws, cudaStream_t s, int shape) {
     static_assert(sizeof(rpca_mat_desc) == sizeof(rpca::Item), "descriptor layout");
     const BatchLayout B = batch_layout(count, max_m, o->l);
     char *base = reinterpret_cast<char *>(ws);
@@ -128,9 +132,11 @@ int run_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, const 
     RPCA_CHECK_LAUNCH();
     rpca::BatchLaunch a{items, order, count, o->l, o->k, o->its, o->raw, o->seed, col_weights, item_status, queue,
                         reinterpret_cast<float *>(base + B.slots), B.slot_floats, max_m, rpca::num_sms(), s};
-    if (rpt == 2) return rpca::launch_batched_r2(a);
-    if (rpt == 8) return rpca::launch_batched_r8(a);
-    return rpca::launch_batched_r4(a);
+    switch (shape) {
+        case 0: return rpca::launch_batched_r2k64(a);
+        case 2: return rpca::launch_batched_r8k32(a);
+        default: return rpca::launch_batched_r4k32(a);
+    }
 }
 
 }  // namespace
@@ -146,22 +152,22 @@ extern "C" int rpca_batched(int32_t count, const rpca_mat_desc *descs, int64_t m
 
 extern "C" int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n,
                                  const rpca_opts *o, const float *const *col_weights, int32_t *item_status, void *ws,
-                                 size_t ws_bytes, rpca_stream_t stream, int32_t *rows_per_thread, float *ms) {
+                                 size_t ws_bytes, rpca_stream_t stream, int32_t *rows_per_thread, int32_t *depth,
+                                 float *ms) {
     RPCA_TRY(check_args(count, descs, max_m, max_n, o, ws, ws_bytes));
     if (count == 0) return RPCA_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int cand[3] = {2, 4, 8};
     float best_ms = 0.f;
-    int best = 4;
+    int best = kDefaultShape;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return RPCA_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return RPCA_ERR_CUDA; }
     int rc = RPCA_OK;
-    for (int c = 0; c < 3 && rc == RPCA_OK; ++c) {
-        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, cand[c]);     // warm-up
+    for (int c = 0; c < kNumShapes && rc == RPCA_OK; ++c) {
+        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c);     // warm-up
         if (rc != RPCA_OK) break;
         if (cudaEventRecord(e0, s) != cudaSuccess) { rc = RPCA_ERR_CUDA; break; }
-        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, cand[c]);
+        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c);
         if (rc != RPCA_OK) break;
         float t = 0.f;
         if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -170,7 +176,7 @@ extern "C" int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int6
             break;
         }
         if (ms) ms[c] = t;
-        if (c == 0 || t < best_ms) { best_ms = t; best = cand[c]; }
+        if (c == 0 || t < best_ms) { best_ms = t; best = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -179,6 +185,7 @@ extern "C" int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int6
         std::lock_guard<std::mutex> g(g_tune_mutex);
         g_tuned[tune_key(count, max_m, max_n, o)] = best;
     }
-    if (rows_per_thread) *rows_per_thread = best;
+    if (rows_per_thread) *rows_per_thread = kShapes[best].rows;
+    if (depth) *depth = kShapes[best].depth;
     return RPCA_OK;
 }

@@ -52,12 +52,13 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kMaxLP = 40;                 // l <= 32
 constexpr int kMaxNL = 24576;              // n * lp floats of the n-side block
-constexpr int kBK = 32;                    // K per A tile
-constexpr int kMaxRPT = 8;                 // rows (A X) or columns (A^T Y) of A per thread
+// pass tiles: RPT rows (A X) or columns (A^T Y) of A per thread, KB deep; the shapes in use
+// are (2, 64), (4, 32) and (8, 32)
 constexpr int kJacSweeps = 30;
 constexpr int kGramGroups = 16;            // row groups of the Gram
 constexpr int kMaxPairs = 64;              // 4x4 blocks of the upper triangle, lp <= 40 -> 55
-constexpr int kPassFloats = kBK * (64 * kMaxRPT + 4) + kBK * kMaxLP;
+constexpr int pass_floats(int rpt, int kb) { return kb * (64 * rpt + 4) + kb * kMaxLP; }
+constexpr int kPassFloats = pass_floats(8, 32) > pass_floats(2, 64) ? pass_floats(8, 32) : pass_floats(2, 64);
 constexpr int kTileFloats = kGramGroups * kMaxPairs * 16 > kPassFloats ? kGramGroups * kMaxPairs * 16 : kPassFloats;
 
 struct Smem {
@@ -73,6 +74,10 @@ struct Smem {
     int flag;
     int item;
 };
+// At most 196 KB of shared memory per CTA: past that the SM switches to its largest
+// carve-out and the L1 cache left next to it (which serves the m-side block Y) drops
+// from ~60 KB to ~28 KB, measured ~10% slower on the kernel-matrix batch.
+static_assert(sizeof(Smem) <= 196 * 1024, "batched shared memory beyond the 196 KB carve-out");
 
 // ---------------------------------------------------------------------------
 // Test matrix of one item: the single-matrix path's stream keyed (seed, 0), element
@@ -118,20 +123,20 @@ __device__ __forceinline__ void load_run(const float *p, float (&v)[RPT]) {
 // Y (m x lp, global) = A X (X = sm.X, n x lp).  Thread: RPT rows x CPT columns (tiles of
 // 64 RPT rows); the next A tile is fetched into registers while the current one is
 // multiplied.  Every output sums over k in order whatever RPT is.
-template <int CPT, int RPT>
+template <int CPT, int RPT, int KB>
 __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int lp,
                          float *__restrict__ Y) {
     constexpr int BM = 64 * RPT, LDT = BM + 4;
-    float *As = sm.tile;                          // [kBK][LDT]
+    float *As = sm.tile;                          // [KB][LDT]
     const int tid = threadIdx.x;
     const int rq = tid >> 3, cg = tid & 7;        // 64 row groups x 8 column groups
-    constexpr int PER = BM * kBK / kThreads;      // elements of a tile per thread
+    constexpr int PER = BM * KB / kThreads;      // elements of a tile per thread
     float pre[PER];
     auto fetch = [&](int64_t r0, int64_t k0) {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int e = tid + q * kThreads;
-            const int r = e / kBK, kk = e % kBK;
+            const int r = e / KB, kk = e % KB;
             const int64_t gr = r0 + r, gk = k0 + kk;
             pre[q] = (gr < m && gk < n) ? __ldg(A + gr * lda + gk) : 0.f;
         }
@@ -140,10 +145,10 @@ __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int e = tid + q * kThreads;
-            As[(e % kBK) * LDT + e / kBK] = pre[q];
+            As[(e % KB) * LDT + e / KB] = pre[q];
         }
     };
-    const int64_t ktiles = (n + kBK - 1) / kBK;
+    const int64_t ktiles = (n + KB - 1) / KB;
     for (int64_t r0 = 0; r0 < m; r0 += BM) {
         float acc[RPT][CPT];
 #pragma unroll
@@ -152,12 +157,12 @@ __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64
             for (int q = 0; q < CPT; ++q) acc[a][q] = 0.f;
         fetch(r0, 0);
         for (int64_t t = 0; t < ktiles; ++t) {
-            const int64_t k0 = t * kBK;
+            const int64_t k0 = t * KB;
             __syncthreads();
             stash();
             __syncthreads();
-            if (t + 1 < ktiles) fetch(r0, k0 + kBK);
-            const int kn = (int)min((int64_t)kBK, n - k0);
+            if (t + 1 < ktiles) fetch(r0, k0 + KB);
+            const int kn = (int)min((int64_t)KB, n - k0);
             for (int kk = 0; kk < kn; ++kk) {
                 float a[RPT];
                 load_run<RPT>(&As[kk * LDT + RPT * rq], a);
@@ -188,16 +193,16 @@ __device__ void apply_ax(Smem &sm, const float *__restrict__ A, int64_t m, int64
 // X (n x lp, shared) = A^T Y (Y global, m x lp).  Thread: RPT columns of A x CPT columns of
 // Y (tiles of 64 RPT columns); the next tiles are fetched into registers while the current
 // ones are multiplied.  Every output sums over the rows in order whatever RPT is.
-template <int CPT, int RPT>
+template <int CPT, int RPT, int KB>
 __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int lp,
                           const float *__restrict__ Y) {
     constexpr int BN = 64 * RPT, LDT = BN + 4;
-    float *As = sm.tile;                          // [kBK][LDT]
-    float *Ys = sm.tile + kBK * LDT;              // [kBK][lp]
+    float *As = sm.tile;                          // [KB][LDT]
+    float *Ys = sm.tile + KB * LDT;              // [KB][lp]
     const int tid = threadIdx.x;
     const int cq = tid >> 3, cg = tid & 7;        // 64 column groups of A x 8 column groups of Y
-    constexpr int PER = BN * kBK / kThreads;
-    float pre[PER], prey[(kBK * kMaxLP + kThreads - 1) / kThreads];
+    constexpr int PER = BN * KB / kThreads;
+    float pre[PER], prey[(KB * kMaxLP + kThreads - 1) / kThreads];
     auto fetch = [&](int64_t c0, int64_t r0) {
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
@@ -207,10 +212,10 @@ __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int6
             pre[q] = (gr < m && gc < n) ? __ldg(A + gr * lda + gc) : 0.f;
         }
 #pragma unroll
-        for (int q = 0; q < (kBK * kMaxLP + kThreads - 1) / kThreads; ++q) {
+        for (int q = 0; q < (KB * kMaxLP + kThreads - 1) / kThreads; ++q) {
             const int e = tid + q * kThreads;
             float v = 0.f;
-            if (e < kBK * lp) {
+            if (e < KB * lp) {
                 const int rr = e / lp;
                 const int64_t gr = r0 + rr;
                 if (gr < m) v = Y[gr * lp + (e - rr * lp)];
@@ -225,12 +230,12 @@ __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int6
             As[(e / BN) * LDT + e % BN] = pre[q];
         }
 #pragma unroll
-        for (int q = 0; q < (kBK * kMaxLP + kThreads - 1) / kThreads; ++q) {
+        for (int q = 0; q < (KB * kMaxLP + kThreads - 1) / kThreads; ++q) {
             const int e = tid + q * kThreads;
-            if (e < kBK * lp) Ys[e] = prey[q];
+            if (e < KB * lp) Ys[e] = prey[q];
         }
     };
-    const int64_t rtiles = (m + kBK - 1) / kBK;
+    const int64_t rtiles = (m + KB - 1) / KB;
     for (int64_t c0 = 0; c0 < n; c0 += BN) {
         float acc[RPT][CPT];
 #pragma unroll
@@ -239,12 +244,12 @@ __device__ void apply_aty(Smem &sm, const float *__restrict__ A, int64_t m, int6
             for (int q = 0; q < CPT; ++q) acc[a][q] = 0.f;
         fetch(c0, 0);
         for (int64_t t = 0; t < rtiles; ++t) {
-            const int64_t r0 = t * kBK;
+            const int64_t r0 = t * KB;
             __syncthreads();
             stash();
             __syncthreads();
-            if (t + 1 < rtiles) fetch(c0, r0 + kBK);
-            const int kn = (int)min((int64_t)kBK, m - r0);
+            if (t + 1 < rtiles) fetch(c0, r0 + KB);
+            const int kn = (int)min((int64_t)KB, m - r0);
             for (int kk = 0; kk < kn; ++kk) {
                 float a[RPT];
                 load_run<RPT>(&As[kk * LDT + RPT * cq], a);
@@ -500,7 +505,7 @@ __device__ void small_svd(Smem &sm, int l) {
 }
 
 // Per item: the method.  Y0 / Y1: this CTA's m-side slots.
-template <int CPT, int RPT>
+template <int CPT, int RPT, int KB>
 __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its, int raw, uint64_t seed,
                          const float *weights, float *Y0, int32_t *status) {
     const float *A = it.A;
@@ -528,7 +533,7 @@ __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its
     };
     // X = A_c^T Y: the ones column l of Y gives m c; subtract c (1^T Y)
     auto adjoint = [&](const float *Y) {
-        apply_aty<CPT, RPT>(sm, A, m, n, lda, lp, Y);
+        apply_aty<CPT, RPT, KB>(sm, A, m, n, lda, lp, Y);
         if (!raw) {
             for (int64_t e = threadIdx.x; e < n * lp; e += blockDim.x) {
                 const int64_t j = e / lp;
@@ -543,7 +548,7 @@ __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its
     };
 
     gen_omega(sm, n, l, lp, seed, weights);
-    apply_ax<CPT, RPT>(sm, A, m, n, lda, lp, Y0);
+    apply_ax<CPT, RPT, KB>(sm, A, m, n, lda, lp, Y0);
     centre_m(Y0);
     for (int it2 = 0; it2 <= its; ++it2) {
         const bool final_ = it2 == its;
@@ -555,7 +560,7 @@ __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its
             adjoint(Y0);
             solve_rows(sm, sm.X, n, l, lp);
             cholqr(sm, sm.X, n, l, lp);
-            apply_ax<CPT, RPT>(sm, A, m, n, lda, lp, Y0);
+            apply_ax<CPT, RPT, KB>(sm, A, m, n, lda, lp, Y0);
             centre_m(Y0);
         } else {
             const bool sh = cholqr(sm, Y0, m, l, lp);
@@ -621,7 +626,7 @@ __device__ __forceinline__ bool item_ok(const Item &it, int l, int k, int64_t ma
            (reinterpret_cast<uintptr_t>(it.A) & 3u) == 0;
 }
 
-template <int CPT, int RPT>
+template <int CPT, int RPT, int KB>
 __global__ void __launch_bounds__(kThreads, 1)
 batched_kernel(const Item *__restrict__ items, const int32_t *__restrict__ order, int count, int l, int k, int its,
                int raw, uint64_t seed, const float *const *__restrict__ weights, int32_t *__restrict__ item_status,
@@ -639,25 +644,26 @@ batched_kernel(const Item *__restrict__ items, const int32_t *__restrict__ order
         const int idx = order ? order[q] : q;
         const Item it = items[idx];
         if (!item_ok(it, l, k, max_m)) continue;          // reported by check_items_kernel
-        run_item<CPT, RPT>(sm, it, l, lp, k, its, raw, seed, weights ? weights[idx] : nullptr, Y0,
+        run_item<CPT, RPT, KB>(sm, it, l, lp, k, its, raw, seed, weights ? weights[idx] : nullptr, Y0,
                       item_status ? item_status + idx : nullptr);
     }
 }
 
 }  // namespace
 
-// One launch of the batched kernel with RPT rows (or columns) of A per thread in the
-// passes; the column count per thread follows from l.
-template <int RPT>
+// One launch of the batched kernel with pass tiles of RPT rows (or columns) of A per
+// thread, KB deep; the column count per thread follows from l.
+template <int RPT, int KB>
 int launch_batched_rpt(const BatchLaunch &a) {
+    static_assert(pass_floats(RPT, KB) <= kPassFloats, "pass tile larger than the shared tile area");
     const int lp = (int)round_up(a.l + 1, 8);
     const size_t smem = sizeof(Smem);
 #define RPCA_BATCH_LAUNCH(CPT)                                                                                    \
     do {                                                                                                          \
-        if (cudaFuncSetAttribute(batched_kernel<CPT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+        if (cudaFuncSetAttribute(batched_kernel<CPT, RPT, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                  (int)smem) != cudaSuccess)                                                        \
             return RPCA_ERR_CUDA;                                                                                 \
-        batched_kernel<CPT, RPT><<<a.grid, kThreads, smem, a.stream>>>(a.items, a.order, a.count, a.l, a.k, a.its, \
+        batched_kernel<CPT, RPT, KB><<<a.grid, kThreads, smem, a.stream>>>(a.items, a.order, a.count, a.l, a.k, a.its, \
                                                                        a.raw, a.seed, a.weights, a.item_status,    \
                                                                        a.queue, a.slots, a.slot_floats, a.max_m);  \
     } while (0)
@@ -671,9 +677,9 @@ int launch_batched_rpt(const BatchLaunch &a) {
     return RPCA_OK;
 }
 
-// instantiated one per translation unit (batched_r2.cu, batched_r4.cu, batched_r8.cu)
-int launch_batched_r2(const BatchLaunch &a);
-int launch_batched_r4(const BatchLaunch &a);
-int launch_batched_r8(const BatchLaunch &a);
+// instantiated one per translation unit (batched_r2k64.cu, batched_r4k32.cu, ...)
+int launch_batched_r2k64(const BatchLaunch &a);
+int launch_batched_r4k32(const BatchLaunch &a);
+int launch_batched_r8k32(const BatchLaunch &a);
 
 }  // namespace rpca

@@ -354,8 +354,9 @@ def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = F
 
 def rpca_batched_tune(batch: Batch, l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
                       col_weights=None, ws: torch.Tensor | None = None, stream=None):
-    """Time the batched kernel's tile shapes on this batch and keep the fastest for later
-    rpca_batched calls on batches of the same shape.  Returns (rows_per_thread, [ms x 3])."""
+    """Time the batched kernel's pass-tile shapes on this batch and keep the fastest for later
+    rpca_batched calls on batches of the same shape.  Returns ((rows_per_thread, depth),
+    [ms for 2x64, 4x32, 8x32])."""
     k = batch.k
     opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr")
     lib = L.load()
@@ -372,11 +373,13 @@ def rpca_batched_tune(batch: Batch, l: int | None = None, its: int = 2, raw: boo
         wptr = weights_table(col_weights, batch.desc.device)
         batch._wkeep = (col_weights, wptr)
     rpt = C.c_int32(0)
+    depth = C.c_int32(0)
     ms = (C.c_float * 3)()
     _check(lib.rpca_batched_tune(count, _ptr(batch.desc), batch.max_m, batch.max_n, C.byref(opts), _ptr(wptr),
-                                 _ptr(batch.status), _ptr(ws), ws.numel(), _stream(stream), C.byref(rpt), ms),
+                                 _ptr(batch.status), _ptr(ws), ws.numel(), _stream(stream), C.byref(rpt),
+                                 C.byref(depth), ms),
            "rpca_batched_tune")
-    return int(rpt.value), [float(x) for x in ms]
+    return (int(rpt.value), int(depth.value)), [float(x) for x in ms]
 
 
 # ---------------------------------------------------------------------------
