@@ -304,9 +304,20 @@ class Batch:
         device = device or mats[0].device
         self.mats = mats
         self.k = k
-        self.U = [torch.empty(a.shape[0], k, dtype=torch.float32, device=device) for a in mats]
-        self.S = [torch.empty(k, dtype=torch.float32, device=device) for _ in mats]
-        self.V = [torch.empty(a.shape[1], k, dtype=torch.float32, device=device) for a in mats]
+        # outputs as views of three contiguous buffers (one copy reads all of them back)
+        mu = [int(a.shape[0]) * k for a in mats]
+        nv = [int(a.shape[1]) * k for a in mats]
+        self.U_all = torch.empty(sum(mu), dtype=torch.float32, device=device)
+        self.S_all = torch.empty(len(mats) * k, dtype=torch.float32, device=device)
+        self.V_all = torch.empty(sum(nv), dtype=torch.float32, device=device)
+        self.U, self.S, self.V = [], [], []
+        ou = ov = 0
+        for i, a in enumerate(mats):
+            self.U.append(self.U_all[ou:ou + mu[i]].view(a.shape[0], k))
+            self.S.append(self.S_all[i * k:(i + 1) * k])
+            self.V.append(self.V_all[ov:ov + nv[i]].view(a.shape[1], k))
+            ou += mu[i]
+            ov += nv[i]
         rows = []
         for a, u, s_, v in zip(mats, self.U, self.S, self.V):
             _need_cuda(a, "A")
