@@ -67,7 +67,8 @@ typedef enum rpca_precision {
 
 typedef enum rpca_renorm {
     RPCA_RENORM_CHOLQR = 0,      /* Gram + Cholesky renormalisation (span-equivalent to LU) */
-    RPCA_RENORM_LU = 1           /* tall-skinny LU with tournament pivoting (Section 5's lu) */
+    RPCA_RENORM_LU = 1           /* tall-skinny LU with tournament pivoting (Section 5's lu);
+                                    dense and CSR with l <= 160, else RPCA_ERR_UNSUPPORTED */
 } rpca_renorm;
 
 typedef struct rpca_opts {

@@ -22,6 +22,7 @@
 // (lanes own columns and sweep the rows bottom-up in lock step); then block
 // rows I = nb-2 .. 0 in turn: S = R[I, >I] X[>I, >I], X[I, >I] = -X[I,I] S.
 #include "internal.cuh"
+#include "gepp.cuh"
 
 namespace rpca {
 
@@ -298,6 +299,52 @@ chol_inv_big_kernel(const double *__restrict__ G, int l, int lp, float *__restri
     chol_finish(R, ld, S, l, lp, Rinv, Racc_in, Racc_out);
 }
 
+// The tall-skinny LU's last step: W = the l pivot rows of Y (ids), partial-pivoting
+// LU W = P L U in shared memory, Rinv = U^-1 (lp x lp).  Missing rows (id < 0) enter
+// as zero rows; a zero or non-finite pivot (Y rank deficient) is replaced by 1 and
+// counted with the shifts, non-finite input is reported.
+__global__ void __launch_bounds__(kRegThreads)
+lu_final_kernel(const float *__restrict__ Y, int64_t rows, int lp, int l, const int32_t *__restrict__ ids_in,
+                float *__restrict__ Rinv, DevStatus *__restrict__ st) {
+    extern __shared__ float sm[];
+    const int ld = l + 1;
+    float *R = sm;
+    float *S = sm + (size_t)l * ld;
+    __shared__ int ids[RPCA_MAX_L];
+    __shared__ GeppScratch g;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_bad = 0;
+    for (int r = tid; r < l; r += nt) {
+        const int id = ids_in[r];
+        ids[r] = (id >= 0 && id < rows) ? id : 0x7fffffff;       // present either way
+    }
+    __syncthreads();
+    for (int e = tid; e < l * l; e += nt) {
+        const int r = e / l, c = e - r * l;
+        const int id = ids[r];
+        const float v = id != 0x7fffffff ? Y[(int64_t)id * lp + c] : 0.f;
+        if (!isfinite(v)) s_bad = 1;
+        R[r * ld + c] = v;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) dev_fail(st, RPCA_ERR_NONFINITE);
+        for (int e = tid; e < lp * lp; e += nt) Rinv[e] = ((e / lp) == (e % lp) && (e / lp) < l) ? 1.f : 0.f;
+        return;
+    }
+    gepp_block(R, ld, ids, l, l, g);
+    for (int j = tid; j < l; j += nt) {
+        const float d = R[j * ld + j];
+        if (d == 0.f || !isfinite(d)) {
+            R[j * ld + j] = 1.f;
+            atomicAdd(&st->shifts, 1);
+        }
+    }
+    __syncthreads();
+    chol_finish(R, ld, S, l, lp, Rinv, nullptr, nullptr);
+}
+
 template <int NS>
 int launch_reg(const double *G, int l, int lp, float *Rinv, const float *Racc_in, float *Racc_out, DevStatus *st,
                cudaStream_t s, int *shifted_out, const int *skip_flag, size_t smem, size_t smem_max) {
@@ -311,6 +358,18 @@ int launch_reg(const double *G, int l, int lp, float *Rinv, const float *Racc_in
 }
 
 }  // namespace
+
+int launch_lu_final(const float *Y, int64_t rows, int lp, int l, const int32_t *ids, float *Rinv, DevStatus *st,
+                    cudaStream_t s) {
+    const size_t smem = ((size_t)l * (l + 1) + (size_t)kNB * (l > kNB ? l - kNB : 1)) * sizeof(float);
+    const size_t smem_max = ((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) + (size_t)kNB * (RPCA_MAX_L - kNB)) * sizeof(float);
+    if (cudaFuncSetAttribute(lu_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
+        cudaSuccess)
+        return RPCA_ERR_CUDA;
+    lu_final_kernel<<<1, kRegThreads, smem, s>>>(Y, rows, lp, l, ids, Rinv, st);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
 
 int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
                     float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out, const int *skip_flag) {

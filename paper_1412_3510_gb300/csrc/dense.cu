@@ -63,7 +63,7 @@ extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, con
     if (!A || !o || lda < n) return RPCA_ERR_INVALID_ARG;
     const size_t need = rpca_dense_workspace_size(m, n, o);
     RPCA_TRY(rpca::check_common(m, n, o, U, ldu, S, V, ldv, ws, ws_bytes, need));
-    if (o->renorm != RPCA_RENORM_CHOLQR) return RPCA_ERR_UNSUPPORTED;
+    if (o->renorm == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
     rpca::DenseOp op;
     op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
     const int lp = rpca::padded_l(o->l);

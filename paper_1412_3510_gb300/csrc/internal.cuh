@@ -80,6 +80,14 @@ int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, 
 int launch_gram(const float *Y, int64_t rows, int lp, float *part, int splits, const int *skip_flag,
                 cudaStream_t s);
 int gram_splits(int64_t rows, int lp);
+// tall-skinny LU with tournament pivoting (renorm = LU): the l pivot rows of Y, then
+// Rinv = U^-1 from the LU of those rows
+size_t tslu_ids_bytes(int64_t rows, int l);
+bool tslu_supported(int l);
+int launch_tslu_select(const float *Y, int64_t rows, int lp, int l, int32_t *buf0, int32_t *buf1,
+                       const int32_t **winner, cudaStream_t s);
+int launch_lu_final(const float *Y, int64_t rows, int lp, int l, const int32_t *ids, float *Rinv, DevStatus *st,
+                    cudaStream_t s);
 
 // Number of K slices launch_sgemm should use so that the grid fills the GPU.
 int choose_splits(int64_t M, int64_t N, int64_t K);

@@ -76,6 +76,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.zbuf = take(256);
     L.rinv_m = take(lp * lp * 4);
     L.flags = take(256);
+    L.lu0 = take(tslu_ids_bytes(std::max(m, n), l));
+    L.lu1 = take(tslu_ids_bytes(std::max(m, n), l));
     L.scratch = take(op_scratch);
     L.total = off;
     return L;
@@ -102,6 +104,7 @@ struct Ctx {
     char *ws;
     cudaStream_t s;
     DevStatus *st;
+    bool lu = false;          // non-final renormalisations by tall-skinny LU
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
 };
 
@@ -119,6 +122,15 @@ int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *ri
     }
     TimedScope ts(kTimeChol, c.s);
     return launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s, shifted_out, skip);
+}
+
+// Tall-skinny LU of a block: rinv = U^-1 with in = P^T L U (tournament pivoting).
+int lu_factor(const Ctx &c, const float *in, int64_t rows, float *rinv) {
+    const Layout &L = c.L;
+    TimedScope ts(kTimeChol, c.s);
+    const int32_t *winner = nullptr;
+    RPCA_TRY(launch_tslu_select(in, rows, L.lp, L.l, c.at<int32_t>(L.lu0), c.at<int32_t>(L.lu1), &winner, c.s));
+    return launch_lu_final(in, rows, L.lp, L.l, winner, rinv, c.st, c.s);
 }
 
 // One CholeskyQR round: out = in R^-1.  With skip (*skip == 0 on the device) the round is
@@ -150,7 +162,8 @@ int renorm_m(const Ctx &c, bool raw, bool final_, const float **q, bool *pending
     }
     float *qout = y1;
     if (!final_) {
-        RPCA_TRY(gram_chol(c, y0, L.m, L.s_gram_m, c.at<float>(L.rinv_m), nullptr, nullptr, nullptr, nullptr));
+        if (c.lu) RPCA_TRY(lu_factor(c, y0, L.m, c.at<float>(L.rinv_m)));
+        else RPCA_TRY(gram_chol(c, y0, L.m, L.s_gram_m, c.at<float>(L.rinv_m), nullptr, nullptr, nullptr, nullptr));
         qout = y0;
         *pending = true;
     } else {
@@ -172,6 +185,12 @@ int renorm_n(const Ctx &c, bool final_) {
     float *x0 = c.at<float>(L.x0), *x1 = c.at<float>(L.x1);
     float *r0 = c.at<float>(L.racc0), *r1 = c.at<float>(L.racc1);
     int *flag = c.at<int>(L.flags) + 1;
+    if (!final_ && c.lu) {
+        float *rinv = c.at<float>(L.rinv);
+        RPCA_TRY(lu_factor(c, x0, L.n, rinv));
+        TimedScope ts(kTimeTrsm, c.s);
+        return launch_sgemm(false, L.n, L.lp, L.lp, x0, L.lp, rinv, L.lp, x1, L.lp, 1, 0, c.s);
+    }
     if (!final_) return cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, nullptr);
     RPCA_TRY(cholqr_round(c, x0, x1, L.n, L.s_gram_n, nullptr, r0, flag));
     RPCA_TRY(cholqr_round(c, x1, x0, L.n, L.s_gram_n, r0, r1));
@@ -204,7 +223,8 @@ int adjoint_pass(const Operator &op, const Ctx &c, bool raw, const float *q, boo
 
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status) {
-    Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status)};
+    Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status),
+          o->renorm == RPCA_RENORM_LU};
     op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
     op.st = c.st;
     const bool raw = o->raw != 0;

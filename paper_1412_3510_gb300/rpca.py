@@ -233,7 +233,8 @@ def _need_i32(t, name):
 def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, shape, k: int,
              l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
              omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
-             ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+             ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
+             renorm: str = "cholqr"):
     """Randomized PCA of a CSR matrix (row_ptr int32 m+1, col_idx int32 nnz, val float32 nnz)."""
     m, n = int(shape[0]), int(shape[1])
     _need_i32(row_ptr, "row_ptr")
@@ -246,7 +247,7 @@ def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, sh
     if col_weights is not None:
         _need_cuda(col_weights, "col_weights")
         col_weights = col_weights.contiguous()
-    opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr", omega, col_weights)
+    opts = make_opts(k, l, its, raw, seed, "fp32", renorm, omega, col_weights)
     lib = L.load()
     need = int(lib.rpca_csr_workspace_size(m, n, nnz, C.byref(opts)))
     if need == 0:

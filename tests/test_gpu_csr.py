@@ -22,11 +22,11 @@ def _dev(csr):
             torch.from_numpy(csr.data.astype(np.float32)).cuda())
 
 
-def _check(csr, k, l, its, raw, seed):
+def _check(csr, k, l, its, raw, seed, **kw):
     cuda()
     import paper_1412_3510_gb300 as rp
     rp_, ci, va = _dev(csr)
-    U, Sg, V = rp.rpca_csr(rp_, ci, va, csr.shape, k, l, its=its, raw=raw, seed=seed)
+    U, Sg, V = rp.rpca_csr(rp_, ci, va, csr.shape, k, l, its=its, raw=raw, seed=seed, **kw)
     Ug, sg, Vg = to_np(U), to_np(Sg), to_np(V)
     Uo, so, Vo = O.rpca(csr, k, l, its, raw=raw, seed=seed)
     assert np.all(np.abs(sg - so) <= 1e-4 * so + 1e-6 * so[0]), (np.abs(sg - so) / so).max()
@@ -41,11 +41,12 @@ def _check(csr, k, l, its, raw, seed):
     assert abs(est - ref) <= 1e-3 * ref
 
 
+@pytest.mark.parametrize("renorm", ["cholqr", "lu"])
 @pytest.mark.parametrize("raw", [True, False])
-def test_powerlaw_csr_parity(raw):
+def test_powerlaw_csr_parity(raw, renorm):
     rp_, ci, va = S.powerlaw_csr(3000, 1500, 40000, exponent=2.1, rank=8, seed=5)
     csr = sp.csr_matrix((va, ci, rp_), shape=(3000, 1500))
-    _check(csr, 8, 10, 3, raw, seed=11)
+    _check(csr, 8, 10, 3, raw, seed=11, renorm=renorm)
 
 
 def test_heavy_rows_and_empty_rows():

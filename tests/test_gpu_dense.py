@@ -69,6 +69,36 @@ def test_dense_parity(m, n, k, l, its, raw, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("m,n,k,l,its,raw", [c for c in CASES if c[3] <= 160] + [(20000, 300, 40, 150, 2, False)])
+def test_dense_lu_renorm_parity(m, n, k, l, its, raw, precision):
+    """Section 5's LU renormalisation (tall-skinny LU, tournament pivoting) against the
+    oracle's partial-pivoting LU: the span after every renormalisation is the same, so
+    the outputs agree to the same bar."""
+    sig = np.exp(-np.arange(1, min(m, n) + 1) / max(4.0, l / 2.0))
+    A = S.haar_dense_np(m, n, sig, seed=m * 7 + n)
+    if not raw:
+        A = A + np.float32(0.3) * np.random.default_rng(m).standard_normal(n).astype(np.float32)[None, :]
+    _check_parity(A, k, l, its, raw, seed=m + n + k, precision=precision, renorm="lu")
+
+
+def test_dense_lu_rank_deficient_and_unsupported_width():
+    cuda()
+    import paper_1412_3510_gb300 as rp
+    # rank 3 with l = 8: the LU meets zero pivots, which count as shifts; the leading
+    # triplets still match the oracle
+    rng = np.random.default_rng(2)
+    A = (rng.standard_normal((700, 3)) @ rng.standard_normal((3, 90))).astype(np.float32)
+    U, Sg, V = rp.rpca_dense(to_dev(A), 3, 8, its=2, raw=True, seed=5, renorm="lu")
+    _, so, _ = O.rpca(A, 3, 8, 2, raw=True, seed=5)
+    assert np.all(np.abs(to_np(Sg) - so) <= 1e-4 * so)
+    # the tall-skinny LU holds 2l x (l + 1) entries per node: l > 160 is refused
+    B = to_dev(rng.standard_normal((400, 200)).astype(np.float32))
+    with pytest.raises(rp.RpcaError) as e:
+        rp.rpca_dense(B, 150, 170, its=1, renorm="lu")
+    assert e.value.code == -7
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_dense_first_workload_full_size(precision):
     w = S.WORKLOADS["dense_2000x1000_k10"]
     A = S.haar_dense_np(w["m"], w["n"], w["spectrum"](min(w["m"], w["n"])), w["seed"])
