@@ -833,10 +833,10 @@ def main():
     if not args.no_forms and not csr:
         side_steps = max(10, min(args.steps, 50))
 
-        def time_form(precision, its_f):
+        def time_form(precision, its_f, renorm="cholqr"):
             def once():
                 rp.rpca_dense(A, k, l, its=its_f, raw=raw, seed=1 + rank, precision=precision, ws=ws,
-                              out=(U, S, V), check=False)
+                              out=(U, S, V), check=False, renorm=renorm)
             for _ in range(args.warmup):
                 once()
             barrier()
@@ -857,6 +857,13 @@ def main():
         ms_fp32 = time_form("fp32", its)
         forms["plain_fp32"] = {"value": world / (ms_fp32 / 1e3), "ms_per_step": ms_fp32, "steps": side_steps,
                                "speedup_of_headline": ms_fp32 / ms_per_step}
+        if l <= 160 and its > 0:
+            # Section 5's LU renormalisation (tall-skinny LU) in place of CholeskyQR
+            ms_lu = time_form(args.precision, its, renorm="lu")
+            est_lu = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
+            forms["lu_renorm"] = {"value": world / (ms_lu / 1e3), "ms_per_step": ms_lu, "steps": side_steps,
+                                  "precision": args.precision, "resid_over_sigma_k1": est_lu / sk1,
+                                  "speedup_of_headline": ms_lu / ms_per_step}
         if est > 1.1 * sk1:
             for its_b in range(its + 1, its + 4):
                 ms_b = time_form(args.precision, its_b)

@@ -19,6 +19,7 @@
 // adjoint product holds ones (it carries m c through A^T), every other padding
 // column holds zeros.
 #include "pipeline.cuh"
+#include "tc_gemm.cuh"
 #include "timing.cuh"
 
 namespace rpca {
@@ -78,6 +79,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.flags = take(256);
     L.lu0 = take(tslu_ids_bytes(std::max(m, n), l));
     L.lu1 = take(tslu_ids_bytes(std::max(m, n), l));
+    L.rsplit = take(tc_rmul_split_bytes(L.lp));
     L.scratch = take(op_scratch);
     L.total = off;
     return L;
@@ -117,7 +119,11 @@ int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *ri
     double *G = c.at<double>(L.G);
     {
         TimedScope ts(kTimeGram, c.s);
-        RPCA_TRY(launch_gram(in, rows, lp, part, splits, skip, c.s));
+        if (tc_gram_ok(rows, lp)) {
+            RPCA_TRY(launch_tc_gram(in, rows, lp, part, &splits, skip, c.st, c.s));
+        } else {
+            RPCA_TRY(launch_gram(in, rows, lp, part, splits, skip, c.s));
+        }
         RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s, skip));
     }
     TimedScope ts(kTimeChol, c.s);
@@ -142,6 +148,8 @@ int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int sp
     float *rinv = c.at<float>(L.rinv);
     RPCA_TRY(gram_chol(c, in, rows, splits, rinv, racc_in, racc_out, shifted_out, skip));
     TimedScope ts(kTimeTrsm, c.s);
+    if (tc_rmul_ok(rows, lp))
+        return launch_tc_rmul(in, rows, lp, rinv, lp, lp, c.at<__nv_bfloat16>(L.rsplit), out, lp, skip, c.st, c.s);
     RPCA_TRY(launch_sgemm(false, rows, lp, lp, in, lp, rinv, lp, out, lp, 1, 0, c.s, skip));
     return RPCA_OK;
 }
@@ -273,6 +281,8 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     TimedScope ts_lift(kTimeLift, s);
     RPCA_TRY(launch_sgemm(false, L.n, L.k, lp, x1, lp, zk, L.kp, V, ldv, 1, 0, s));
     RPCA_TRY(launch_sign_fix(V, L.n, ldv, L.k, wk, lp, L.kp, sig, S, s));
+    if (tc_rmul_ok(L.m, L.k) && (reinterpret_cast<uintptr_t>(U) & 3u) == 0)
+        return launch_tc_rmul(y1, L.m, lp, wk, L.kp, L.k, c.at<__nv_bfloat16>(L.rsplit), U, ldu, nullptr, c.st, s);
     RPCA_TRY(launch_sgemm(false, L.m, L.k, lp, y1, lp, wk, L.kp, U, ldu, 1, 0, s));
     return RPCA_OK;
 }

@@ -21,6 +21,11 @@
 //                the other, FP32 stores
 // Every wait on an mbarrier is bounded; a wait that runs out records
 // RPCA_ERR_TIMEOUT in the status block and the CTA drains and exits.
+//
+// The same kernel serves the tall-skinny products of the renormalisations
+// (Gram matrices Y^T Y and Y R^-1) with a three-piece split a = hi + mid + lo
+// (exact) and the six products of order <= 2^-18, which is as accurate as FP32
+// arithmetic: for the Gram the converted tile of Y is both MMA operands.
 #include "internal.cuh"
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -45,18 +50,19 @@ constexpr int kChunkRows = 2048;
 constexpr int kStagesA = 3;           // FP32 A ring depth
 constexpr int kBufs = 2;              // converted BF16 buffers
 
-// Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).
-template <int BK>
+// Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).  NS BF16
+// pieces per operand; GRAM: the B operand is the A operand (no B buffers).
+template <int BK, int NS, bool GRAM>
 struct Plan {
     static constexpr uint32_t a32_bytes = kBM * BK * 4;          // FP32 stage
-    static constexpr uint32_t abf_bytes = kBM * BK * 2;          // one of hi / lo
-    uint32_t b_bytes;                                            // one of hi / lo (N x BK bf16)
+    static constexpr uint32_t abf_bytes = kBM * BK * 2;          // one piece of A
+    uint32_t b_bytes;                                            // one piece of B (N x BK bf16)
     uint32_t off_a32, off_buf, buf_bytes, off_bar, total;
     __host__ __device__ explicit Plan(int N) {
-        b_bytes = (uint32_t)N * BK * 2;
+        b_bytes = GRAM ? 0u : (uint32_t)N * BK * 2;
         off_a32 = 0;
         off_buf = kStagesA * a32_bytes;
-        buf_bytes = 2 * abf_bytes + 2 * b_bytes;
+        buf_bytes = NS * abf_bytes + NS * b_bytes;
         off_bar = off_buf + kBufs * buf_bytes;
         total = off_bar + 256;
     }
@@ -76,6 +82,7 @@ struct TcArgs {
     int ntiles;                   // row_tiles x splits
     DevStatus *st;
     int chunk_st;                 // K stages per TMEM accumulation chain
+    const int *skip;              // optional: the launch does nothing when *skip == 0
 };
 
 constexpr int kThreads = 512;     // 16 warps
@@ -83,12 +90,16 @@ constexpr int kConvWarps = 8;     // warps 8..15
 constexpr int kEpiWarp0 = 4;      // warps 4..7
 
 // ADJ = false: out[128 rows of A] = A X.  ADJ = true: out[128 columns of A] = A^T Q
-// over the rows of one split.  Persistent: CTA b takes tiles b, b + gridDim.x, ...
-template <int BK, bool ADJ>
+// over the rows of one split (GRAM: Q = A, N <= 128).  Persistent: CTA b takes
+// tiles b, b + gridDim.x, ...
+template <int BK, bool ADJ, int NS, bool GRAM>
 __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
+    static_assert(NS == 2 || NS == 3, "two or three BF16 pieces");
+    static_assert(!GRAM || ADJ, "the Gram form is an adjoint product");
+    if (args.skip && *args.skip == 0) return;                  // uniform: before any setup
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const Plan<BK> P(args.N);
+    const Plan<BK, NS, GRAM> P(args.N);
     uint64_t *full_a = reinterpret_cast<uint64_t *>(smem + P.off_bar);
     uint64_t *empty_a = full_a + kStagesA;
     uint64_t *full_c = empty_a + kStagesA;
@@ -105,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
-        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], kConvWarps + 1); mbar_init(&empty_c[b], 1); }
+        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM ? 0 : 1)); mbar_init(&empty_c[b], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tm_full[a], 1); mbar_init(&tm_empty[a], 4); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         }
     } else if (warp == 2) {
         // ---------------- block operand producer (bulk copies) ----------------
-        if (lane == 0) {
+        if (!GRAM && lane == 0) {
             uint32_t g = 0;
             for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
                 int64_t row0, kbeg;
@@ -176,9 +187,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                     const int b = g % kBufs;
                     if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
                     uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
-                    const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * 2 * N * BK;
-                    mbar_arrive_tx(&full_c[b], 2 * P.b_bytes);
-                    bulk_load(buf + 2 * P.abf_bytes, src, 2 * P.b_bytes, &full_c[b]);
+                    const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * NS * N * BK;
+                    mbar_arrive_tx(&full_c[b], NS * P.b_bytes);
+                    bulk_load(buf + NS * P.abf_bytes, src, NS * P.b_bytes, &full_c[b]);
                 }
             }
         }
@@ -205,15 +216,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                     if (!mbar_wait(&full_c[b], (g / kBufs) & 1, abort_flag)) { fail(); break; }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
-                    const uint32_t a_hi = base, a_lo = base + P.abf_bytes;
-                    const uint32_t b_hi = base + 2 * P.abf_bytes, b_lo = b_hi + P.b_bytes;
+                    // piece p of A at base + p * abf_bytes; of B after the NS pieces of A
+                    // (GRAM: B = A)
+                    const uint32_t bbase = GRAM ? base : base + NS * P.abf_bytes;
+                    const uint32_t bstep = GRAM ? P.abf_bytes : P.b_bytes;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t o = kk * 256;
                         const uint32_t acc0 = (kc > 0 || kk > 0) ? 1u : 0u;
-                        umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, acc0);
-                        umma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), idesc, 1u);
-                        umma_bf16(d, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), idesc, 1u);
+                        // products of order <= 2^-9 (NS = 2) or <= 2^-18 (NS = 3): pieces (i, j), i + j < NS
+#pragma unroll
+                        for (int q = 0; q < (NS == 2 ? 3 : 6); ++q) {
+                            const int pi = NS == 2 ? (q == 2 ? 1 : 0) : (q < 3 ? (q == 2 ? 1 : 0) : q - 3);
+                            const int pj = NS == 2 ? (q == 1 ? 1 : 0) : (q < 3 ? (q == 1 ? 1 : 0) : 5 - q);
+                            umma_bf16(d, smem_desc(base + pi * P.abf_bytes + o, LBO, SBO),
+                                      smem_desc(bbase + pj * bstep + o, LBO, SBO), idesc, q == 0 ? acc0 : 1u);
+                        }
                     }
                     umma_commit(&empty_c[b]);
                 }
@@ -288,7 +306,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
                 const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
                 uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
-                uint8_t *dhi = buf, *dlo = buf + P.abf_bytes;
                 // core matrices 16 (M) x BK/8 (K); 8 threads per core matrix (one row each)
                 constexpr int tasks = (kBM / 8) * (BK / 8) * 8;
 #pragma unroll
@@ -321,11 +338,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                                                                      (jc & 3) * 4);
                         }
                     }
-                    uint4 hi, lo;
-                    split8(x, hi, lo);
                     const uint32_t off = (uint32_t)(mi * (BK / 8) + ki) * 128 + rr * 16;
-                    *reinterpret_cast<uint4 *>(dhi + off) = hi;
-                    *reinterpret_cast<uint4 *>(dlo + off) = lo;
+                    if (NS == 2) {
+                        uint4 hi, lo;
+                        split8(x, hi, lo);
+                        *reinterpret_cast<uint4 *>(buf + off) = hi;
+                        *reinterpret_cast<uint4 *>(buf + P.abf_bytes + off) = lo;
+                    } else {
+                        uint4 hi, mid, lo;
+                        split8x3(x, hi, mid, lo);
+                        *reinterpret_cast<uint4 *>(buf + off) = hi;
+                        *reinterpret_cast<uint4 *>(buf + P.abf_bytes + off) = mid;
+                        *reinterpret_cast<uint4 *>(buf + 2 * P.abf_bytes + off) = lo;
+                    }
                 }
                 fence_async_smem();
                 __syncwarp();
@@ -354,10 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 }
 
 // ---------------------------------------------------------------------------
-// block operand: FP32 P (rows x ld) -> per stage of BK rows, hi then lo, each
-// N x BK BF16 in K-major core matrices ((n/8) * (BK/8) + k/8) * 64 + (n%8) * 8 + k%8.
+// block operand: FP32 P (rows x ld) -> per stage of BK rows, the NS pieces (hi, lo
+// or hi, mid, lo) one after the other, each N x BK BF16 in K-major core matrices
+// ((n/8) * (BK/8) + k/8) * 64 + (n%8) * 8 + k%8.
 // ---------------------------------------------------------------------------
-template <int BK>
+template <int BK, int NS>
 __global__ void __launch_bounds__(256)
 split_block_kernel(const float *__restrict__ P, int64_t rows, int ncols, int64_t ld, int N,
                    __nv_bfloat16 *__restrict__ out, int64_t nstages) {
@@ -377,12 +403,20 @@ split_block_kernel(const float *__restrict__ P, int64_t rows, int ncols, int64_t
             const int64_t i = s * BK + ki * 8 + e;
             x[e] = (i < rows && col < ncols) ? P[i * ld + col] : 0.f;
         }
-        uint4 hi, lo;
-        split8(x, hi, lo);
-        __nv_bfloat16 *base = out + s * 2 * (int64_t)N * BK;
+        __nv_bfloat16 *base = out + s * NS * (int64_t)N * BK;
         const int64_t off = ((int64_t)(ni * (BK / 8) + ki) * 64 + rr * 8);
-        *reinterpret_cast<uint4 *>(base + off) = hi;
-        *reinterpret_cast<uint4 *>(base + (int64_t)N * BK + off) = lo;
+        if (NS == 2) {
+            uint4 hi, lo;
+            split8(x, hi, lo);
+            *reinterpret_cast<uint4 *>(base + off) = hi;
+            *reinterpret_cast<uint4 *>(base + (int64_t)N * BK + off) = lo;
+        } else {
+            uint4 hi, mid, lo;
+            split8x3(x, hi, mid, lo);
+            *reinterpret_cast<uint4 *>(base + off) = hi;
+            *reinterpret_cast<uint4 *>(base + (int64_t)N * BK + off) = mid;
+            *reinterpret_cast<uint4 *>(base + 2 * (int64_t)N * BK + off) = lo;
+        }
     }
 }
 
@@ -412,11 +446,11 @@ int make_map(CUtensorMap *map, const float *A, int64_t m, int64_t n, int64_t lda
     return r == CUDA_SUCCESS ? RPCA_OK : RPCA_ERR_CUDA;
 }
 
-template <int BK, bool ADJ>
+template <int BK, bool ADJ, int NS = 2, bool GRAM = false>
 int launch_pass(const CUtensorMap &map, const TcArgs &a, dim3 grid, cudaStream_t s) {
-    const Plan<BK> P(a.N);
+    const Plan<BK, NS, GRAM> P(a.N);
     const size_t smem = P.total + 1024;
-    auto kern = tc_pass_kernel<BK, ADJ>;
+    auto kern = tc_pass_kernel<BK, ADJ, NS, GRAM>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RPCA_ERR_CUDA;
     kern<<<grid, kThreads, smem, s>>>(map, a);
@@ -463,9 +497,9 @@ int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cu
     const int64_t chunks = nst * (N / 8) * (BK / 8) * 8;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(cdiv(chunks, 256), (int64_t)num_sms() * 8));
     if (BK == 64)
-        split_block_kernel<64><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
+        split_block_kernel<64, 2><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
     else
-        split_block_kernel<32><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
+        split_block_kernel<32, 2><<<(unsigned)grid, 256, 0, s>>>(P, rows, lp, lp, N, out, nst);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
@@ -476,7 +510,7 @@ int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __n
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
     const int tiles = (int)cdiv(m, kBM);
-    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK)};
+    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK), nullptr};
     dim3 grid((unsigned)std::min(tiles, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
 }
@@ -488,9 +522,73 @@ int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const _
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, (uint32_t)BK));
     const int64_t per = round_up(cdiv(m, splits), BK);
     const int rt = (int)cdiv(n, kBM);
-    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st, std::max(1, kChunkRows / BK)};
+    TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st, std::max(1, kChunkRows / BK),
+             nullptr};
     dim3 grid((unsigned)std::min(rt * splits, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
+}
+
+// ---------------------------------------------------------------------------
+// renormalisation products in three-piece split BF16
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kRmulBK = 32;             // K stage of Y R^-1 (K = lp is short)
+
+// out = Y when *flag == 0 (a skipped product is the identity), else nothing
+__global__ void __launch_bounds__(256) copy_if_skipped_kernel(const int *__restrict__ flag, const float4 *__restrict__ src,
+                                                              float4 *__restrict__ dst, int64_t n4) {
+    if (*flag != 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+constexpr int kGramChainStages = 4;     // 256 rows per TMEM chain: drift <= 2e-6 on Y^T Y
+}  // namespace
+
+bool tc_gram_ok(int64_t rows, int lp) { return rows >= kTcRenormMinRows && tc_n(lp) <= kBM; }
+bool tc_rmul_ok(int64_t rows, int ncols) { return rows >= kTcRenormMinRows && tc_n(ncols) <= 256; }
+
+size_t tc_rmul_split_bytes(int lp) {
+    return (size_t)cdiv(lp, kRmulBK) * 3 * tc_n(lp) * kRmulBK * sizeof(__nv_bfloat16);
+}
+
+int launch_tc_gram(const float *Y, int64_t rows, int lp, float *part, int *splits_out, const int *skip,
+                   DevStatus *st, cudaStream_t s) {
+    if (!tc_gram_ok(rows, lp)) return RPCA_ERR_INVALID_ARG;
+    const int N = tc_n(lp);
+    constexpr int BK = 64;
+    const int splits = tc_adjoint_splits(lp, rows, lp);
+    CUtensorMap map;
+    RPCA_TRY(make_map(&map, Y, rows, lp, lp, 32, (uint32_t)BK));
+    const int64_t per = round_up(cdiv(rows, splits), BK);
+    TcArgs a{nullptr, part, lp, lp, lp, N, per, rows, (int64_t)lp * lp, 1, splits, st, kGramChainStages, skip};
+    *splits_out = splits;
+    return launch_pass<BK, true, 3, true>(map, a, dim3((unsigned)std::min(splits, num_sms()), 1, 1), s);
+}
+
+int launch_tc_rmul(const float *Y, int64_t rows, int lp, const float *R, int64_t ldr, int ncols,
+                   __nv_bfloat16 *rsplit, float *out, int64_t ldo, const int *skip, DevStatus *st, cudaStream_t s) {
+    if (!tc_rmul_ok(rows, ncols) || ncols > lp) return RPCA_ERR_INVALID_ARG;
+    const int N = tc_n(ncols);
+    constexpr int BK = kRmulBK;
+    const int64_t nst = cdiv(lp, BK);
+    const int64_t chunks = nst * (N / 8) * (BK / 8) * 8;
+    split_block_kernel<BK, 3><<<(unsigned)cdiv(chunks, 256), 256, 0, s>>>(R, lp, ncols, ldr, N, rsplit, nst);
+    RPCA_CHECK_LAUNCH();
+    CUtensorMap map;
+    RPCA_TRY(make_map(&map, Y, rows, lp, lp, 32, kBM));
+    const int tiles = (int)cdiv(rows, kBM);
+    TcArgs a{rsplit, out, rows, ldo, ncols, N, lp, lp, 0, tiles, tiles, st, std::max(1, kChunkRows / BK), skip};
+    RPCA_TRY((launch_pass<BK, false, 3, false>(map, a, dim3((unsigned)std::min(tiles, num_sms()), 1, 1), s)));
+    if (skip) {
+        // a skipped round is the identity: out = Y (square R, out shaped like Y)
+        if (ncols != lp || ldo != lp) return RPCA_ERR_INVALID_ARG;
+        const int64_t n4 = rows * (int64_t)lp / 4;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(cdiv(n4, 256), (int64_t)num_sms() * 4));
+        copy_if_skipped_kernel<<<(unsigned)grid, 256, 0, s>>>(skip, reinterpret_cast<const float4 *>(Y),
+                                                              reinterpret_cast<float4 *>(out), n4);
+        RPCA_CHECK_LAUNCH();
+    }
+    return RPCA_OK;
 }
 
 }  // namespace rpca

@@ -22,4 +22,21 @@ int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __n
 int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *qsplit, int lp,
                       float *part, int splits, DevStatus *st, cudaStream_t s);
 
+// The renormalisations' tall-skinny products on the tensor cores, split in three
+// BF16 pieces (exact) with the six products of order <= 2^-18: FP32 accuracy.
+constexpr int64_t kTcRenormMinRows = 16384;            // shorter blocks stay on the SIMT kernels
+bool tc_gram_ok(int64_t rows, int lp);                 // lp <= 128
+bool tc_rmul_ok(int64_t rows, int ncols);              // ncols <= 256
+size_t tc_rmul_split_bytes(int lp);
+// part[s] (lp x lp) = Y^T Y over the rows of split s (*splits_out of them); nothing
+// when skip && *skip == 0.
+int launch_tc_gram(const float *Y, int64_t rows, int lp, float *part, int *splits_out, const int *skip,
+                   DevStatus *st, cudaStream_t s);
+// out (rows x ncols, leading dimension ldo) = Y R with Y rows x lp (leading dimension
+// lp) and R lp x ncols (leading dimension ldr), ncols <= lp; R is split into rsplit
+// (tc_rmul_split_bytes(lp) bytes).  With skip (square R, ncols == ldo == lp) the
+// product is the identity when *skip == 0: out = Y, as launch_sgemm's copy flag.
+int launch_tc_rmul(const float *Y, int64_t rows, int lp, const float *R, int64_t ldr, int ncols,
+                   __nv_bfloat16 *rsplit, float *out, int64_t ldo, const int *skip, DevStatus *st, cudaStream_t s);
+
 }  // namespace rpca

@@ -115,5 +115,26 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Split 8 floats into three BF16 octets with x = hi + mid + lo exactly (each
+// difference is exact in FP32 by Sterbenz's lemma; 8 + 8 + 8 significant bits).
+__device__ __forceinline__ void split8x3(const float (&x)[8], uint4 &hi, uint4 &mid, uint4 &lo) {
+    uint32_t h[4], md[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 hb = __float22bfloat162_rn(make_float2(x[2 * e], x[2 * e + 1]));
+        const float2 hf = __bfloat1622float2(hb);
+        const float2 r = make_float2(x[2 * e] - hf.x, x[2 * e + 1] - hf.y);
+        const __nv_bfloat162 mb = __float22bfloat162_rn(r);
+        const float2 mf = __bfloat1622float2(mb);
+        const __nv_bfloat162 lb = __float22bfloat162_rn(make_float2(r.x - mf.x, r.y - mf.y));
+        h[e] = bf2_bits(hb);
+        md[e] = bf2_bits(mb);
+        l[e] = bf2_bits(lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    mid = make_uint4(md[0], md[1], md[2], md[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 }  // namespace ptx
 }  // namespace rpca

@@ -49,6 +49,13 @@ def test_powerlaw_csr_parity(raw, renorm):
     _check(csr, 8, 10, 3, raw, seed=11, renorm=renorm)
 
 
+def test_tall_csr_parity():
+    """60000 rows: the m-side renormalisations run on the tensor cores."""
+    rp_, ci, va = S.powerlaw_csr(60000, 2000, 300000, exponent=2.1, rank=6, seed=8)
+    csr = sp.csr_matrix((va, ci, rp_), shape=(60000, 2000))
+    _check(csr, 6, 10, 2, False, seed=3)
+
+
 def test_heavy_rows_and_empty_rows():
     # rows with many more than 2048 nonzeros (split into chunks), empty rows, a column of A^T > 2048
     rng = np.random.default_rng(9)

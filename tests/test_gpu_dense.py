@@ -68,6 +68,48 @@ def test_dense_parity(m, n, k, l, its, raw, precision):
     _check_parity(A, k, l, its, raw, seed=m + n + k, precision=precision)
 
 
+# tall blocks (>= 16384 rows): the renormalisations' Gram matrices and Y R^-1 products
+# and the U lift run on the tensor cores in three-piece split BF16; lp <= 128 takes the
+# tensor-core Gram, wider blocks the SIMT Gram with the tensor-core products
+TALL_CASES = [
+    (20000, 300, 40, 50, 2, False),
+    (33333, 500, 100, 120, 1, False),     # lp = 128, the widest tensor-core Gram
+    (16384, 200, 10, 12, 3, True),
+    (40000, 257, 150, 160, 1, False),     # lp = 168: SIMT Gram, tensor-core products
+    (17001, 300, 5, 8, 0, True),          # its = 0
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("m,n,k,l,its,raw", TALL_CASES)
+def test_dense_tall_parity(m, n, k, l, its, raw, precision):
+    sig = np.exp(-np.arange(1, min(m, n) + 1) / max(4.0, l / 2.0))
+    A = S.haar_dense_np(m, n, sig, seed=m * 7 + n)
+    if not raw:
+        A = A + np.float32(0.3) * np.random.default_rng(m).standard_normal(n).astype(np.float32)[None, :]
+    _check_parity(A, k, l, its, raw, seed=m + n + k, precision=precision)
+
+
+@pytest.mark.parametrize("raw", [True, False])
+def test_exact_low_rank_recovery_tall(raw):
+    """Rank r < l on 20000 rows: the final CholeskyQR shifts and runs its third round
+    on the tensor cores (and skips it in the other case, an identity copy)."""
+    cuda()
+    import paper_1412_3510_gb300 as rp
+    rng = np.random.default_rng(5)
+    r = 9 if raw else 8
+    A = (rng.standard_normal((20000, r)) @ rng.standard_normal((r, 300))).astype(np.float32)
+    if not raw:
+        A += np.float32(2.0)
+    for l in (11, 9):
+        U, Sg, V = rp.rpca_dense(to_dev(A), 9, l, its=1, raw=raw, seed=4)
+        Ac = A.astype(np.float64) - (0 if raw else A.astype(np.float64).mean(0))
+        E = Ac - (to_np(U) * to_np(Sg)) @ to_np(V).T
+        assert np.linalg.norm(E, 2) / np.linalg.norm(Ac, 2) < 2e-6, l
+        Ug = to_np(U)
+        assert np.linalg.norm(Ug.T @ Ug - np.eye(9), 2) < 1e-4
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("m,n,k,l,its,raw", [c for c in CASES if c[3] <= 160] + [(20000, 300, 40, 150, 2, False)])
 def test_dense_lu_renorm_parity(m, n, k, l, its, raw, precision):
