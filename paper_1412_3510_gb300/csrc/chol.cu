@@ -10,14 +10,9 @@
 // SIAM J. Sci. Comput. 42 (2020)), the product with an accumulated triangular
 // factor (for B^* = Q2 R2), and the triangular inverse used by the next GEMM.
 //
-// Cholesky, right-looking: step j takes pivot row j, a_jk (k >= j), and updates
-// a_ik -= (a_ji / a_jj) a_jk for j < i <= k; row j of R is a_jk / sqrt(a_jj).
-//  - l <= 180: every thread keeps a fixed set of upper-triangle entries (the
-//    flattened triangle dealt out cyclically) in registers for the whole
-//    factorization; the pivot row is double-buffered in shared memory, so a
-//    step is one barrier and a few FMAs per thread.
-//  - larger l: the entries live in shared memory; warp w updates rows
-//    j+1+w, j+33+w, ... with its lanes along the row, one barrier per step.
+// Cholesky, right-looking and blocked by 32 (see chol_blocked_kernel): a warp
+// factors each diagonal block in registers, the panel to its right is solved
+// against it, and the trailing upper triangle is updated in 4 x 4 tiles.
 // Inverse: blocked by 32.  Each warp inverts one 32 x 32 diagonal block
 // (lanes own columns and sweep the rows bottom-up in lock step); then block
 // rows I = nb-2 .. 0 in turn: S = R[I, >I] X[>I, >I], X[I, >I] = -X[I,I] S.
@@ -28,9 +23,7 @@ namespace rpca {
 
 namespace {
 
-constexpr int kRegThreads = 512;
-constexpr int kBigThreads = 1024;
-constexpr int kRegMaxL = 180;          // l (l + 1) / 2 <= 32 entries per thread
+constexpr int kLuThreads = 512;
 constexpr int kNB = 32;
 
 // sum_{t < n} a[t * sa] b[t * sb] with four independent partial sums
@@ -65,20 +58,6 @@ __device__ bool chol_skip(const int *skip_flag, int l, int lp, float *Rinv, cons
     return true;
 }
 
-// finiteness of G, its diagonal and the largest diagonal entry
-__device__ void chol_scan(const double *G, int l, CholShared &cs) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) { cs.bad = 0; cs.maxdiag = 0.f; }
-    __syncthreads();
-    for (int e = tid; e < l * l; e += nt)
-        if (!isfinite(G[e])) cs.bad = 1;
-    for (int j = tid; j < l; j += nt) {
-        cs.dorig[j] = (float)G[(size_t)j * l + j];
-        atomicMax(reinterpret_cast<int *>(&cs.maxdiag), __float_as_int(fmaxf(cs.dorig[j], 0.f)));
-    }
-    __syncthreads();
-}
-
 // the factorization failed even after the shifts: report, R = I
 __device__ void chol_fail(bool bad, DevStatus *st, int l, int lp, float *Rinv, float *Racc_out) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -88,13 +67,11 @@ __device__ void chol_fail(bool bad, DevStatus *st, int l, int lp, float *Rinv, f
         for (int e = tid; e < l * l; e += nt) Racc_out[e] = (e / l == e % l) ? 1.f : 0.f;
 }
 
-// R (upper, shared memory, row stride ld) -> Racc_out = R Racc_in (or R), then R^-1
-// in place and Rinv (lp x lp, zero padded).  S: kNB x (l - kNB) scratch.
-__device__ void chol_finish(float *R, int ld, float *S, int l, int lp, float *__restrict__ Rinv,
-                            const float *__restrict__ Racc_in, float *__restrict__ Racc_out) {
+// Racc_out = R Racc_in (or R) from the upper triangle of R (shared memory, row
+// stride ld).
+__device__ void chol_racc(const float *R, int ld, int l, const float *__restrict__ Racc_in,
+                          float *__restrict__ Racc_out) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
-    const int lds = l > kNB ? l - kNB : 1;
     if (Racc_out) {
         for (int e = tid; e < l * l; e += nt) {
             const int i = e / l, k = e - i * l;
@@ -104,8 +81,44 @@ __device__ void chol_finish(float *R, int ld, float *S, int l, int lp, float *__
             Racc_out[e] = v;
         }
     }
+}
+
+// Block rows I = nb-2 .. 0 of X = R^-1 in place, the diagonal blocks already
+// inverted: S[i][c] = sum_t R[r0+i][t] X[t][c], X[r0+i][c] = -sum_s X[r0+i][r0+s] S[s][c].
+// S: kNB x (l - kNB) scratch.  Then Rinv (lp x lp, zero padded).
+__device__ void chol_inv_rows(float *R, int ld, float *S, int l, int lp, float *__restrict__ Rinv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lds = l > kNB ? l - kNB : 1;
+    const int nb = (l + kNB - 1) / kNB;
+    for (int I = nb - 2; I >= 0; --I) {
+        const int r0 = I * kNB, c0 = r0 + kNB;       // block row [r0, c0), columns [c0, l)
+        const int w = l - c0;
+        for (int e = tid; e < kNB * w; e += nt) {
+            const int i = e / w, cc = e - i * w, c = c0 + cc;
+            S[i * lds + cc] = dot4(R + (r0 + i) * ld + c0, 1, R + c0 * ld + c, ld, c - c0 + 1);
+        }
+        __syncthreads();
+        for (int e = tid; e < kNB * w; e += nt) {
+            const int i = e / w, cc = e - i * w;
+            R[(r0 + i) * ld + c0 + cc] = -dot4(R + (r0 + i) * ld + r0 + i, 1, S + i * lds + cc, lds, kNB - i);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < lp * lp; e += nt) {
+        const int i = e / lp, k = e - i * lp;
+        Rinv[e] = (i < l && k < l && k >= i) ? R[i * ld + k] : 0.f;
+    }
+}
+
+// R (upper, shared memory, row stride ld) -> Racc_out = R Racc_in (or R), then R^-1
+// in place and Rinv (lp x lp, zero padded).  S: kNB x (l - kNB) scratch.
+__device__ void chol_finish(float *R, int ld, float *S, int l, int lp, float *__restrict__ Rinv,
+                            const float *__restrict__ Racc_in, float *__restrict__ Racc_out) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+    chol_racc(R, ld, l, Racc_in, Racc_out);
     __syncthreads();
-    // step A: diagonal blocks, one warp each
+    // diagonal blocks, one warp each
     const int nb = (l + kNB - 1) / kNB;
     for (int b = warp; b < nb; b += nwarps) {
         const int b0 = b * kNB, bl = min(kNB, l - b0);
@@ -121,25 +134,7 @@ __device__ void chol_finish(float *R, int ld, float *S, int l, int lp, float *__
         }
     }
     __syncthreads();
-    // step B: block rows bottom-up
-    for (int I = nb - 2; I >= 0; --I) {
-        const int r0 = I * kNB, c0 = r0 + kNB;       // block row [r0, c0), columns [c0, l)
-        const int w = l - c0;
-        for (int e = tid; e < kNB * w; e += nt) {    // S[i][c] = sum_{t = c0}^{c} R[r0+i][t] X[t][c]
-            const int i = e / w, cc = e - i * w, c = c0 + cc;
-            S[i * lds + cc] = dot4(R + (r0 + i) * ld + c0, 1, R + c0 * ld + c, ld, c - c0 + 1);
-        }
-        __syncthreads();
-        for (int e = tid; e < kNB * w; e += nt) {    // X[r0+i][c] = -sum_{s >= i} X[r0+i][r0+s] S[s][c]
-            const int i = e / w, cc = e - i * w;
-            R[(r0 + i) * ld + c0 + cc] = -dot4(R + (r0 + i) * ld + r0 + i, 1, S + i * lds + cc, lds, kNB - i);
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < lp * lp; e += nt) {
-        const int i = e / lp, k = e - i * lp;
-        Rinv[e] = (i < l && k < l && k >= i) ? R[i * ld + k] : 0.f;
-    }
+    chol_inv_rows(R, ld, S, l, lp, Rinv);
 }
 
 __device__ __forceinline__ float next_shift(float shift, int l, float maxdiag) {
@@ -147,81 +142,275 @@ __device__ __forceinline__ float next_shift(float shift, int l, float maxdiag) {
 }
 
 // ---------------------------------------------------------------------------
-// l <= 180: entries in registers.  Thread t owns entries e = t + s * blockDim.x
-// (s < NS) of the upper triangle flattened row by row.
+// Blocked right-looking Cholesky, panels of 32 columns, the whole matrix in shared
+// memory (row stride ld = round_up(l, 4), so that rows are 16-byte aligned):
+//   1. warp 0 factors the 32 x 32 diagonal block in registers: lane c holds column
+//      c; pivot j is broadcast by shuffles, no CTA barrier inside the block;
+//   2. the panel R[J, >J] = R[J,J]^-T A[J, >J]: one thread per column, forward
+//      substitution with the diagonal block read by broadcast;
+//   3. the trailing update A[>J, >J] -= R[J, >J]^T R[J, >J] in 4 x 4 register tiles
+//      of the upper triangle.
+// Three barriers per panel instead of one per pivot.
 // ---------------------------------------------------------------------------
-template <int NS>
-__global__ void __launch_bounds__(kRegThreads, 1)
-chol_inv_reg_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
+constexpr int kBlkThreads = 512;
+
+__host__ __device__ __forceinline__ int chol_ld(int l) { return (l + 3) & ~3; }
+
+// Block rows of X = R^-1 (ld a multiple of 4, diagonal blocks already inverted) in
+// 4 x 4 register tiles; the strictly lower triangle is cleared first so that every
+// sum runs over whole tiles.  S: kNB x (ld - kNB) scratch.  Then Rinv (lp x lp).
+__device__ void chol_inv_rows_tiled(float *R, int ld, float *S, int l, int lp, float *__restrict__ Rinv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+    for (int i = warp; i < ld; i += nwarps)
+        for (int k = lane; k < i; k += 32) R[i * ld + k] = 0.f;
+    __syncthreads();
+    const int nb = (l + kNB - 1) / kNB;
+    for (int I = nb - 2; I >= 0; --I) {
+        const int r0 = I * kNB, c0 = r0 + kNB;
+        const int lds = ld - c0, wq = lds / 4;
+        // S[i][cc] = sum_{c0 <= t <= c} R[r0+i][t] X[t][c], c = c0 + cc
+        for (int q = tid; q < (kNB / 4) * wq; q += nt) {
+            const int iq = q / wq, cq = q - iq * wq;
+            const int i0 = r0 + 4 * iq, cc0 = 4 * cq;
+            float acc[4][4] = {};
+            const int tend = c0 + cc0 + 4;
+            for (int t = c0; t < tend; ++t) {
+                const float4 v = *reinterpret_cast<const float4 *>(R + t * ld + c0 + cc0);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float u = R[(i0 + x) * ld + t];
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(u, vv[y], acc[x][y]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                *reinterpret_cast<float4 *>(S + (4 * iq + x) * lds + cc0) =
+                    make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+        }
+        __syncthreads();
+        // X[r0+i][c] = -sum_{s >= i} X[r0+i][r0+s] S[s][c - c0]
+        for (int q = tid; q < (kNB / 4) * wq; q += nt) {
+            const int iq = q / wq, cq = q - iq * wq;
+            const int i0 = 4 * iq, cc0 = 4 * cq;
+            float acc[4][4] = {};
+            for (int sr = i0; sr < kNB; ++sr) {
+                const float4 v = *reinterpret_cast<const float4 *>(S + sr * lds + cc0);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float u = R[(r0 + i0 + x) * ld + r0 + sr];
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(u, vv[y], acc[x][y]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                *reinterpret_cast<float4 *>(R + (r0 + i0 + x) * ld + c0 + cc0) =
+                    make_float4(-acc[x][0], -acc[x][1], -acc[x][2], -acc[x][3]);
+        }
+        __syncthreads();
+    }
+    for (int i = warp; i < lp; i += nwarps)
+        for (int k = lane; k < lp; k += 32) Rinv[(size_t)i * lp + k] = (i < l && k < l && k >= i) ? R[i * ld + k] : 0.f;
+}
+
+// A (ld x ld) = G + shift I (zero padding), with the finiteness of G, its diagonal
+// and its largest diagonal entry in cs (first call).
+__device__ void chol_load(const double *__restrict__ G, int l, int ld, float shift, float *A, CholShared &cs,
+                          bool first) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    constexpr int kBatch = 8;                     // independent loads in flight per thread
+    bool bad = false;
+    const int total = ld * ld;
+    for (int base = tid; base < total; base += nt * kBatch) {
+        double g[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int e = base + b * nt, i = e / ld, k = e - i * ld;
+            g[b] = (e < total && i < l && k < l) ? G[(size_t)i * l + k] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int e = base + b * nt, i = e / ld, k = e - i * ld;
+            if (e < total) {
+                bad |= !isfinite(g[b]);
+                float v = (float)g[b];
+                if (i == k && i < l) {
+                    if (first) {
+                        cs.dorig[i] = v;
+                        atomicMax(reinterpret_cast<int *>(&cs.maxdiag), __float_as_int(fmaxf(v, 0.f)));
+                    }
+                    v += shift;
+                }
+                A[e] = v;
+            }
+        }
+    }
+    if (first && __any_sync(0xffffffffu, bad) && lane == 0) cs.bad = 1;
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 1)
+chol_blocked_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
                     const float *__restrict__ Racc_in, float *__restrict__ Racc_out, DevStatus *__restrict__ st,
                     int *__restrict__ shifted_out, const int *__restrict__ skip_flag) {
-    extern __shared__ float sm[];
-    const int ld = l + 1;
-    float *R = sm;                        // l x ld (upper triangle used)
-    float *S = sm + (size_t)l * ld;
+    extern __shared__ float4 sm4[];
+    float *A = reinterpret_cast<float *>(sm4);
+    const int ld = chol_ld(l);
+    float *S = A + (size_t)ld * ld;
     __shared__ CholShared cs;
-    __shared__ float rowbuf[2][RPCA_MAX_L];
+    __shared__ float rdinv[RPCA_MAX_L];           // 1 / R_jj of the factored panels
     __shared__ int s_broke;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
     if (chol_skip(skip_flag, l, lp, Rinv, Racc_in, Racc_out, shifted_out)) return;
-    chol_scan(G, l, cs);
-    const bool bad = cs.bad != 0;
-
-    // this thread's entries: row i, column k (k >= i); unused slots get i = k = l
-    int si[NS], sk[NS];
-    const int T = l * (l + 1) / 2;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const int e = tid + s * nt;
-        int i = l, k = l;
-        if (e < T) {
-            // rows before i hold off(i) = i (2l - i + 1) / 2 entries; solve off(i) <= e
-            const float b = 2.f * l + 1.f;
-            i = (int)((b - sqrtf(fmaxf(b * b - 8.f * e, 0.f))) * 0.5f);
-            i = max(0, min(i, l - 1));
-            while (i + 1 < l && (i + 1) * (2 * l - i) / 2 <= e) ++i;
-            while (i > 0 && i * (2 * l - i + 1) / 2 > e) --i;
-            k = i + (e - i * (2 * l - i + 1) / 2);
-        }
-        si[s] = i;
-        sk[s] = k;
-    }
+    if (tid == 0) { cs.bad = 0; cs.maxdiag = 0.f; }
+    __syncthreads();
 
     const float tau = 16.f * (float)l * 0x1p-24f;     // a pivot below tau * G_jj has collapsed
     float shift = 0.f;
     bool ok = false;
-    for (int attempt = 0; attempt < 4 && !bad; ++attempt) {
-        float a[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            a[s] = 0.f;
-            if (sk[s] < l) {
-                a[s] = (float)G[(size_t)si[s] * l + sk[s]];
-                if (si[s] == sk[s]) a[s] += shift;
-                if (si[s] == 0) rowbuf[0][sk[s]] = a[s];
-            }
-        }
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        chol_load(G, l, ld, shift, A, cs, attempt == 0);
         if (tid == 0) s_broke = 0;
         __syncthreads();
-        for (int j = 0; j < l; ++j) {
-            const float *rb = rowbuf[j & 1];
-            float *rn = rowbuf[(j + 1) & 1];
-            const float d = rb[j];
-            if (!(d > tau * cs.dorig[j] + 0.5f * shift) || !(d > 0.f)) {   // uniform: every thread reads d
-                if (tid == 0) s_broke = 1;
-                break;
-            }
-            const float inv_d = 1.0f / d;
-            const float inv_r = rsqrtf(d);
-            for (int t = tid; t < l - j; t += nt) R[j * ld + j + t] = t == 0 ? d * inv_r : rb[j + t] * inv_r;
-            // slots run in increasing row order, so the finished ones (row <= j) form a
-            // prefix: walk down from the last slot and stop at the first finished one
+        if (cs.bad) break;
+        for (int b0 = 0; b0 < l; b0 += kNB) {
+            const int bl = min(kNB, l - b0);
+            // 1. diagonal block (rows and columns b0 .. b0 + bl - 1): factor, then its
+            //    inverse X (column c of X in lane c); R goes to the upper triangle, the
+            //    strictly upper part of X transposed to the strictly lower triangle
+            if (warp == 0) {
+                const int c = lane;
+                float a[kNB];
 #pragma unroll
-            for (int s = NS - 1; s >= 0; --s) {
-                if (si[s] <= j) break;
-                if (sk[s] < l) {
-                    a[s] = fmaf(-(rb[si[s]] * inv_d), rb[sk[s]], a[s]);
-                    if (si[s] == j + 1) rn[sk[s]] = a[s];
+                for (int r = 0; r < kNB; ++r) a[r] = (r <= c && c < bl) ? A[(b0 + r) * ld + b0 + c] : 0.f;
+                const float thr = c < bl ? tau * cs.dorig[b0 + c] + 0.5f * shift : 0.f;
+                bool fail = false;
+                float rd = 1.f;                             // this lane's R_cc
+#pragma unroll
+                for (int j = 0; j < kNB; ++j) {
+                    const float d = __shfl_sync(0xffffffffu, a[j], j);
+                    const float t = __shfl_sync(0xffffffffu, thr, j);
+                    const bool good = j >= bl || (d > t && d > 0.f);
+                    fail |= !good;                          // uniform: every lane sees d
+                    a[j] *= rsqrtf(j < bl && good ? d : 1.f);   // row j of R: r_jc (lane j: sqrt(d))
+                    if (lane == j) rd = a[j];
+                    // constant trip counts (r > j resolved at compile time) keep a[] in registers
+#pragma unroll
+                    for (int r = 0; r < kNB; ++r) {
+                        if (r > j) {
+                            const float v = __shfl_sync(0xffffffffu, a[j], r);      // r_jr
+                            if (c >= r) a[r] = fmaf(-v, a[j], a[r]);
+                        }
+                    }
+                }
+                if (fail) {
+                    if (lane == 0) s_broke = 1;
+                } else {
+                    const float rdi = c < bl ? 1.0f / rd : 0.f;
+                    // R x = e_c from the bottom: x_i = ([i == c] - sum_{t > i} r_it x_t) / r_ii
+                    float x[kNB];
+#pragma unroll
+                    for (int i = kNB - 1; i >= 0; --i) {
+                        float s0 = (i == c) ? 1.f : 0.f, s1 = 0.f;       // two chains of FMAs
+#pragma unroll
+                        for (int t = 0; t < kNB; ++t) {
+                            if (t > i) {
+                                const float v = __shfl_sync(0xffffffffu, a[i], t);
+                                if (t & 1) s1 = fmaf(-v, x[t], s1);
+                                else s0 = fmaf(-v, x[t], s0);
+                            }
+                        }
+                        x[i] = (s0 + s1) * __shfl_sync(0xffffffffu, rdi, i);
+                    }
+#pragma unroll
+                    for (int r = 0; r < kNB; ++r) {
+                        if (c < bl && r < c) {
+                            A[(b0 + r) * ld + b0 + c] = a[r];
+                            A[(b0 + c) * ld + b0 + r] = x[r];
+                        }
+                    }
+                    if (c < bl) {
+                        A[(b0 + c) * ld + b0 + c] = rd;
+                        rdinv[b0 + c] = rdi;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_broke) break;
+            const int c0 = b0 + kNB;
+            if (c0 >= l) break;
+            // 2. panel rows b0 .. b0 + 31, columns c0 .. l - 1 (bl = 32 here):
+            //    R[J, c] = X_JJ^T A[J, c]
+            //    four lanes per column, each with 8 of the 32 terms of every row; the
+            //    partial sums meet by shuffles and the panel goes to S (row stride
+            //    lds = ld - c0, padding columns zero) for the trailing update
+            const int lds = ld - c0, w = l - c0;
+            for (int base = 0; base < 4 * lds; base += nt) {   // uniform trip count
+                const int task = base + tid;
+                const int cc = task >> 2, p = task & 3;
+                const bool live = cc < w;
+                float x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] = live ? A[(b0 + 8 * p + i) * ld + c0 + cc] : 0.f;
+                float y[kNB];
+#pragma unroll
+                for (int r = 0; r < kNB; ++r) {
+                    const float *xr = A + (b0 + r) * ld + b0;      // row r: X[t][r] at column t < r
+                    float acc = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int t = 8 * p + i;
+                        const float coef = t < r ? xr[t] : (t == r ? rdinv[b0 + r] : 0.f);
+                        acc = fmaf(coef, x[i], acc);
+                    }
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    y[r] = acc;
+                }
+                if (cc < lds) {
+#pragma unroll
+                    for (int r = 0; r < kNB; ++r)
+                        if ((r & 3) == p) S[r * lds + cc] = live ? y[r] : 0.f;
+                }
+            }
+            __syncthreads();
+            // 3. trailing update of the upper triangle, 4 x 4 tiles (padding rows and
+            //    columns of A are zero and stay zero)
+            for (int e = tid; e < kNB * w; e += nt) {          // the panel back to rows b0 .. b0 + 31
+                const int r = e / w, cc = e - r * w;
+                A[(b0 + r) * ld + c0 + cc] = S[r * lds + cc];
+            }
+            const int wq = lds / 4;
+            const int ntile = wq * (wq + 1) / 2;
+            for (int q = tid; q < ntile; q += nt) {
+                int bi = 0, rem = q;
+                while (rem >= wq - bi) { rem -= wq - bi; ++bi; }
+                const int i0 = c0 + 4 * bi, k0 = c0 + 4 * (bi + rem);
+                float acc[4][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 8
+                for (int t = 0; t < kNB; ++t) {
+                    const float4 u = *reinterpret_cast<const float4 *>(S + t * lds + (i0 - c0));
+                    const float4 v = *reinterpret_cast<const float4 *>(S + t * lds + (k0 - c0));
+                    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(uu[x], vv[y], acc[x][y]);
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    float4 *row = reinterpret_cast<float4 *>(A + (i0 + x) * ld + k0);
+                    float4 w = *row;
+                    w.x -= acc[x][0]; w.y -= acc[x][1]; w.z -= acc[x][2]; w.w -= acc[x][3];
+                    *row = w;
                 }
             }
             __syncthreads();
@@ -232,78 +421,26 @@ chol_inv_reg_kernel(const double *__restrict__ G, int l, int lp, float *__restri
         if (tid == 0) atomicAdd(&st->shifts, 1);
         __syncthreads();
     }
-    if (shifted_out && tid == 0) *shifted_out = (shift != 0.f || !ok) ? 1 : 0;
-    if (!ok) { chol_fail(bad, st, l, lp, Rinv, Racc_out); return; }
-    chol_finish(R, ld, S, l, lp, Rinv, Racc_in, Racc_out);
-}
-
-// ---------------------------------------------------------------------------
-// larger l: entries in shared memory.  The scaled pivot row goes to the
-// (otherwise unused) lower triangle so that the trailing update of the same step
-// can still read the unscaled row; the factor is copied back up at the end.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBigThreads)
-chol_inv_big_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
-                    const float *__restrict__ Racc_in, float *__restrict__ Racc_out, DevStatus *__restrict__ st,
-                    int *__restrict__ shifted_out, const int *__restrict__ skip_flag) {
-    extern __shared__ float sm[];
-    const int ld = l + 1;
-    float *R = sm;
-    float *S = sm + (size_t)l * ld;
-    __shared__ CholShared cs;
-    __shared__ float rdiag[RPCA_MAX_L];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
-    if (chol_skip(skip_flag, l, lp, Rinv, Racc_in, Racc_out, shifted_out)) return;
-    chol_scan(G, l, cs);
     const bool bad = cs.bad != 0;
-
-    const float tau = 16.f * (float)l * 0x1p-24f;
-    float shift = 0.f;
-    bool ok = false;
-    for (int attempt = 0; attempt < 4 && !bad; ++attempt) {
-        for (int e = tid; e < l * l; e += nt) {
-            const int i = e / l, k = e - i * l;
-            float v = (float)G[e];
-            if (i == k) v += shift;
-            R[i * ld + k] = v;
-        }
-        __syncthreads();
-        bool broke = false;
-        for (int j = 0; j < l; ++j) {
-            const float d = R[j * ld + j];
-            if (!(d > tau * cs.dorig[j] + 0.5f * shift) || !(d > 0.f)) { broke = true; break; }
-            const float inv_d = 1.0f / d;
-            const float inv_r = rsqrtf(d);
-            for (int i = j + 1 + warp; i < l; i += nwarps) {
-                const float rji = R[j * ld + i] * inv_d;
-                for (int k = i + lane; k < l; k += 32) R[i * ld + k] = fmaf(-rji, R[j * ld + k], R[i * ld + k]);
-            }
-            for (int k = j + 1 + tid; k < l; k += nt) R[k * ld + j] = R[j * ld + k] * inv_r;
-            if (tid == 0) rdiag[j] = d * inv_r;
-            __syncthreads();
-        }
-        if (!broke) { ok = true; break; }
-        __syncthreads();
-        shift = next_shift(shift, l, cs.maxdiag);
-        if (tid == 0) atomicAdd(&st->shifts, 1);
-    }
     if (shifted_out && tid == 0) *shifted_out = (shift != 0.f || !ok) ? 1 : 0;
     if (!ok) { chol_fail(bad, st, l, lp, Rinv, Racc_out); return; }
-    for (int e = tid; e < l * l; e += nt) {          // the factor back to the upper triangle
-        const int i = e / l, k = e - i * l;
-        if (k > i) R[i * ld + k] = R[k * ld + i];
-        else if (k == i) R[i * ld + i] = rdiag[i];
+    chol_racc(A, ld, l, Racc_in, Racc_out);
+    __syncthreads();
+    // diagonal blocks of X = R^-1 from the strictly lower triangle (transposed) and rdinv
+    for (int e = tid; e < l * kNB; e += nt) {
+        const int i = e / kNB, c = (i / kNB) * kNB + (e % kNB);
+        if (c < l && c > i) A[i * ld + c] = A[c * ld + i];
+        else if (c == i) A[i * ld + i] = rdinv[i];
     }
     __syncthreads();
-    chol_finish(R, ld, S, l, lp, Rinv, Racc_in, Racc_out);
+    chol_inv_rows_tiled(A, ld, S, l, lp, Rinv);
 }
 
 // The tall-skinny LU's last step: W = the l pivot rows of Y (ids), partial-pivoting
 // LU W = P L U in shared memory, Rinv = U^-1 (lp x lp).  Missing rows (id < 0) enter
 // as zero rows; a zero or non-finite pivot (Y rank deficient) is replaced by 1 and
 // counted with the shifts, non-finite input is reported.
-__global__ void __launch_bounds__(kRegThreads)
+__global__ void __launch_bounds__(kLuThreads)
 lu_final_kernel(const float *__restrict__ Y, int64_t rows, int lp, int l, const int32_t *__restrict__ ids_in,
                 float *__restrict__ Rinv, DevStatus *__restrict__ st) {
     extern __shared__ float sm[];
@@ -345,18 +482,6 @@ lu_final_kernel(const float *__restrict__ Y, int64_t rows, int lp, int l, const 
     chol_finish(R, ld, S, l, lp, Rinv, nullptr, nullptr);
 }
 
-template <int NS>
-int launch_reg(const double *G, int l, int lp, float *Rinv, const float *Racc_in, float *Racc_out, DevStatus *st,
-               cudaStream_t s, int *shifted_out, const int *skip_flag, size_t smem, size_t smem_max) {
-    if (cudaFuncSetAttribute(chol_inv_reg_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
-        cudaSuccess)
-        return RPCA_ERR_CUDA;
-    chol_inv_reg_kernel<NS><<<1, kRegThreads, smem, s>>>(G, l, lp, Rinv, Racc_in, Racc_out, st, shifted_out,
-                                                         skip_flag);
-    RPCA_CHECK_LAUNCH();
-    return RPCA_OK;
-}
-
 }  // namespace
 
 int launch_lu_final(const float *Y, int64_t rows, int lp, int l, const int32_t *ids, float *Rinv, DevStatus *st,
@@ -366,33 +491,23 @@ int launch_lu_final(const float *Y, int64_t rows, int lp, int l, const int32_t *
     if (cudaFuncSetAttribute(lu_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
         cudaSuccess)
         return RPCA_ERR_CUDA;
-    lu_final_kernel<<<1, kRegThreads, smem, s>>>(Y, rows, lp, l, ids, Rinv, st);
+    lu_final_kernel<<<1, kLuThreads, smem, s>>>(Y, rows, lp, l, ids, Rinv, st);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
 
 int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
                     float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out, const int *skip_flag) {
+    if (l < 1 || l > RPCA_MAX_L) return RPCA_ERR_INVALID_ARG;
     auto bytes = [](int ll) {
-        return ((size_t)ll * (ll + 1) + (size_t)kNB * (ll > kNB ? ll - kNB : 1)) * sizeof(float);
+        return ((size_t)chol_ld(ll) * chol_ld(ll) + (size_t)kNB * (chol_ld(ll) > kNB ? chol_ld(ll) - kNB : 4)) *
+               sizeof(float);
     };
-    const size_t smem = bytes(l), smem_max = bytes(RPCA_MAX_L);
-    if (l <= kRegMaxL) {
-        const int per = (int)cdiv((int64_t)l * (l + 1) / 2, (int64_t)kRegThreads);
-#define RPCA_CHOL_REG(NS) launch_reg<NS>(G, l, lp, Rinv, Racc_in, Racc_out, st, s, shifted_out, skip_flag, smem, smem_max)
-        if (per <= 2) return RPCA_CHOL_REG(2);
-        if (per <= 4) return RPCA_CHOL_REG(4);
-        if (per <= 8) return RPCA_CHOL_REG(8);
-        if (per <= 12) return RPCA_CHOL_REG(12);
-        if (per <= 16) return RPCA_CHOL_REG(16);
-        if (per <= 24) return RPCA_CHOL_REG(24);
-        return RPCA_CHOL_REG(32);
-#undef RPCA_CHOL_REG
-    }
-    if (cudaFuncSetAttribute(chol_inv_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(chol_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes(RPCA_MAX_L)) != cudaSuccess)
         return RPCA_ERR_CUDA;
-    chol_inv_big_kernel<<<1, kBigThreads, smem, s>>>(G, l, lp, Rinv, Racc_in, Racc_out, st, shifted_out, skip_flag);
+    chol_blocked_kernel<<<1, kBlkThreads, bytes(l), s>>>(G, l, lp, Rinv, Racc_in, Racc_out, st, shifted_out,
+                                                         skip_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
