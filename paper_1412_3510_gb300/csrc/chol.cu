@@ -153,6 +153,7 @@ __device__ __forceinline__ float next_shift(float shift, int l, float maxdiag) {
 // Three barriers per panel instead of one per pivot.
 // ---------------------------------------------------------------------------
 constexpr int kBlkThreads = 512;
+constexpr int kXdLd = kNB + 4;                    // row stride of the diagonal block's inverse
 
 __host__ __device__ __forceinline__ int chol_ld(int l) { return (l + 3) & ~3; }
 
@@ -217,43 +218,32 @@ __device__ void chol_inv_rows_tiled(float *R, int ld, float *S, int l, int lp, f
         for (int k = lane; k < lp; k += 32) Rinv[(size_t)i * lp + k] = (i < l && k < l && k >= i) ? R[i * ld + k] : 0.f;
 }
 
-// A (ld x ld) = G + shift I (zero padding), with the finiteness of G, its diagonal
-// and its largest diagonal entry in cs (first call).
-__device__ void chol_load(const double *__restrict__ G, int l, int ld, float shift, float *A, CholShared &cs,
+// A (ld x ld) = G + shift I from the padded Gram (same layout, zero padding), with
+// the finiteness of G, its diagonal and its largest diagonal entry in cs (first call).
+__device__ void chol_load(const float *__restrict__ G, int l, int ld, float shift, float *A, CholShared &cs,
                           bool first) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-    constexpr int kBatch = 8;                     // independent loads in flight per thread
     bool bad = false;
-    const int total = ld * ld;
-    for (int base = tid; base < total; base += nt * kBatch) {
-        double g[kBatch];
-#pragma unroll
-        for (int b = 0; b < kBatch; ++b) {
-            const int e = base + b * nt, i = e / ld, k = e - i * ld;
-            g[b] = (e < total && i < l && k < l) ? G[(size_t)i * l + k] : 0.0;
+    const int total4 = ld * ld / 4;
+    for (int e4 = tid; e4 < total4; e4 += nt) {
+        const float4 g = reinterpret_cast<const float4 *>(G)[e4];
+        bad |= !(isfinite(g.x) && isfinite(g.y) && isfinite(g.z) && isfinite(g.w));
+        reinterpret_cast<float4 *>(A)[e4] = g;
+    }
+    __syncthreads();
+    for (int i = tid; i < l; i += nt) {
+        const float v = A[i * ld + i];
+        if (first) {
+            cs.dorig[i] = v;
+            atomicMax(reinterpret_cast<int *>(&cs.maxdiag), __float_as_int(fmaxf(v, 0.f)));
         }
-#pragma unroll
-        for (int b = 0; b < kBatch; ++b) {
-            const int e = base + b * nt, i = e / ld, k = e - i * ld;
-            if (e < total) {
-                bad |= !isfinite(g[b]);
-                float v = (float)g[b];
-                if (i == k && i < l) {
-                    if (first) {
-                        cs.dorig[i] = v;
-                        atomicMax(reinterpret_cast<int *>(&cs.maxdiag), __float_as_int(fmaxf(v, 0.f)));
-                    }
-                    v += shift;
-                }
-                A[e] = v;
-            }
-        }
+        A[i * ld + i] = v + shift;
     }
     if (first && __any_sync(0xffffffffu, bad) && lane == 0) cs.bad = 1;
 }
 
 __global__ void __launch_bounds__(kBlkThreads, 1)
-chol_blocked_kernel(const double *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
+chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restrict__ Rinv,
                     const float *__restrict__ Racc_in, float *__restrict__ Racc_out, DevStatus *__restrict__ st,
                     int *__restrict__ shifted_out, const int *__restrict__ skip_flag) {
     extern __shared__ float4 sm4[];
@@ -262,6 +252,7 @@ chol_blocked_kernel(const double *__restrict__ G, int l, int lp, float *__restri
     float *S = A + (size_t)ld * ld;
     __shared__ CholShared cs;
     __shared__ float rdinv[RPCA_MAX_L];           // 1 / R_jj of the factored panels
+    __shared__ __align__(16) float Xd[kNB * kXdLd];   // inverse of the current diagonal block
     __shared__ int s_broke;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -332,6 +323,7 @@ chol_blocked_kernel(const double *__restrict__ G, int l, int lp, float *__restri
                             A[(b0 + r) * ld + b0 + c] = a[r];
                             A[(b0 + c) * ld + b0 + r] = x[r];
                         }
+                        Xd[r * kXdLd + c] = (c < bl && r <= c) ? x[r] : 0.f;
                     }
                     if (c < bl) {
                         A[(b0 + c) * ld + b0 + c] = rd;
@@ -345,41 +337,28 @@ chol_blocked_kernel(const double *__restrict__ G, int l, int lp, float *__restri
             if (c0 >= l) break;
             // 2. panel rows b0 .. b0 + 31, columns c0 .. l - 1 (bl = 32 here):
             //    R[J, c] = X_JJ^T A[J, c]
-            //    four lanes per column, each with 8 of the 32 terms of every row; the
-            //    partial sums meet by shuffles and the panel goes to S (row stride
-            //    lds = ld - c0, padding columns zero) for the trailing update
+            //    as 4 x 4 register tiles of X_JJ^T A[J, >J] into S (row stride
+            //    lds = ld - c0; padding columns of A are zero, so are those of S)
             const int lds = ld - c0, w = l - c0;
-            for (int base = 0; base < 4 * lds; base += nt) {   // uniform trip count
-                const int task = base + tid;
-                const int cc = task >> 2, p = task & 3;
-                const bool live = cc < w;
-                float x[8];
+            for (int q = tid; q < (kNB / 4) * (lds / 4); q += nt) {
+                const int rq = q / (lds / 4), cq = q - rq * (lds / 4);
+                float acc[4][4] = {};
+#pragma unroll 8
+                for (int t = 0; t < kNB; ++t) {
+                    const float4 u = *reinterpret_cast<const float4 *>(Xd + t * kXdLd + 4 * rq);
+                    const float4 v = *reinterpret_cast<const float4 *>(A + (b0 + t) * ld + c0 + 4 * cq);
+                    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] = live ? A[(b0 + 8 * p + i) * ld + c0 + cc] : 0.f;
-                float y[kNB];
+                    for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int r = 0; r < kNB; ++r) {
-                    const float *xr = A + (b0 + r) * ld + b0;      // row r: X[t][r] at column t < r
-                    float acc = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int t = 8 * p + i;
-                        const float coef = t < r ? xr[t] : (t == r ? rdinv[b0 + r] : 0.f);
-                        acc = fmaf(coef, x[i], acc);
-                    }
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                    y[r] = acc;
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(uu[x], vv[y], acc[x][y]);
                 }
-                if (cc < lds) {
 #pragma unroll
-                    for (int r = 0; r < kNB; ++r)
-                        if ((r & 3) == p) S[r * lds + cc] = live ? y[r] : 0.f;
-                }
+                for (int x = 0; x < 4; ++x)
+                    *reinterpret_cast<float4 *>(S + (4 * rq + x) * lds + 4 * cq) =
+                        make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
             }
             __syncthreads();
-            // 3. trailing update of the upper triangle, 4 x 4 tiles (padding rows and
-            //    columns of A are zero and stay zero)
             for (int e = tid; e < kNB * w; e += nt) {          // the panel back to rows b0 .. b0 + 31
                 const int r = e / w, cc = e - r * w;
                 A[(b0 + r) * ld + c0 + cc] = S[r * lds + cc];
@@ -496,7 +475,7 @@ int launch_lu_final(const float *Y, int64_t rows, int lp, int l, const int32_t *
     return RPCA_OK;
 }
 
-int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
+int launch_chol_inv(const float *G, int l, int lp, float *Rinv, const float *Racc_in,
                     float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out, const int *skip_flag) {
     if (l < 1 || l > RPCA_MAX_L) return RPCA_ERR_INVALID_ARG;
     auto bytes = [](int ll) {

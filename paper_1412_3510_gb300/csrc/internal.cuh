@@ -107,8 +107,11 @@ int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, 
 int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value, float *part,
                     cudaStream_t s);
 
-// G (FP64, l x l) = sum over splits of the FP32 partial Grams part[s] (lp x lp).
-int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s,
+// Row stride of the reduced Gram matrix: l rounded up to a multiple of 4.
+__host__ __device__ inline int gram_ld(int l) { return (l + 3) & ~3; }
+// G (FP32, gram_ld(l) x gram_ld(l), zero padding) = compensated sum over splits of the
+// FP32 partial Grams part[s] (lp x lp).
+int launch_gram_reduce(const float *part, int splits, int l, int lp, float *G, cudaStream_t s,
                        const int *skip_flag = nullptr);
 
 // X = sum_s part[s] (rows x lp); when centring, X[:, c] -= (X[:, l] / m) * qsum[c]
@@ -121,7 +124,7 @@ int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, in
 // shifted_out (optional) receives 1 when the diagonal had to be shifted.
 // When skip_flag is given and *skip_flag == 0, R = I: Rinv = I and
 // Racc_out = Racc_in.
-int launch_chol_inv(const double *G, int l, int lp, float *Rinv, const float *Racc_in,
+int launch_chol_inv(const float *G, int l, int lp, float *Rinv, const float *Racc_in,
                     float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out = nullptr,
                     const int *skip_flag = nullptr);
 

@@ -65,7 +65,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.part = take(part * 4);
     L.cpart = take((size_t)L.cchunks * l * 4);
     L.qpart = take((size_t)L.cchunks * l * 4);
-    L.G = take((size_t)l * l * 8);
+    L.G = take((size_t)gram_ld(l) * gram_ld(l) * 4);
     L.rinv = take(lp * lp * 4);
     L.racc0 = take((size_t)l * l * 4);
     L.racc1 = take((size_t)l * l * 4);
@@ -116,7 +116,7 @@ int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *ri
     const Layout &L = c.L;
     const int lp = L.lp;
     float *part = c.at<float>(L.part);
-    double *G = c.at<double>(L.G);
+    float *G = c.at<float>(L.G);
     {
         TimedScope ts(kTimeGram, c.s);
         if (tc_gram_ok(rows, lp)) {

@@ -87,16 +87,18 @@ center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
 // (threadIdx.y): every load is a coalesced 128-byte row of a partial, eight
 // independent chains per entry; the eight group sums are combined in order.
 __global__ void __launch_bounds__(256)
-gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, double *__restrict__ G,
+gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, float *__restrict__ G,
                    const int *__restrict__ skip_flag) {
     if (skip_flag && *skip_flag == 0) return;
     __shared__ float sh[8][32], ch[8][32];
-    const int64_t total = (int64_t)l * l;
+    const int ldg = gram_ld(l);
+    const int64_t total = (int64_t)ldg * ldg;
     const int64_t e = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int y = threadIdx.y;
+    const int a = (int)(e / ldg), b = (int)(e % ldg);
+    const bool in = e < total && a < l && b < l;
     float s = 0.f, comp = 0.f;
-    if (e < total) {
-        const int a = (int)(e / l), b = (int)(e % l);
+    if (in) {
         const float *p = part + (int64_t)a * lp + b;
         const int64_t stride = (int64_t)lp * lp;
         for (int q = y; q < splits; q += 8) {
@@ -117,7 +119,7 @@ gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, do
             c = (u - t) - v;
             t = u;
         }
-        G[e] = (double)t;
+        G[e] = in ? t : 0.f;
     }
 }
 
@@ -203,10 +205,10 @@ int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, 
     return RPCA_OK;
 }
 
-int launch_gram_reduce(const float *part, int splits, int l, int lp, double *G, cudaStream_t s,
+int launch_gram_reduce(const float *part, int splits, int l, int lp, float *G, cudaStream_t s,
                        const int *skip_flag) {
-    gram_reduce_kernel<<<(unsigned)cdiv((int64_t)l * l, (int64_t)32), dim3(32, 8), 0, s>>>(part, splits, l, lp, G,
-                                                                                         skip_flag);
+    const int64_t total = (int64_t)gram_ld(l) * gram_ld(l);
+    gram_reduce_kernel<<<(unsigned)cdiv(total, (int64_t)32), dim3(32, 8), 0, s>>>(part, splits, l, lp, G, skip_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
