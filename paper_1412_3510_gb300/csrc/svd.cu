@@ -8,8 +8,8 @@
 // The l x l SVD is one-sided Jacobi (Hestenes; Demmel & Veselic 1992): plane
 // rotations applied on the right orthogonalise the columns of M = R^T.  One
 // CTA holds M in shared memory (column j of M is row j of R, contiguous) and
-// runs the l/2 disjoint rotations of a round-robin step in parallel, four
-// lanes per column pair.  The rotations are logged; a second kernel replays
+// runs the l/2 disjoint rotations of a round-robin step in parallel, four or
+// eight lanes per column pair.  The rotations are logged; a second kernel replays
 // them on the rows of the identity (every row of Z evolves independently, one
 // warp per row), which keeps Z out of the Jacobi CTA's shared memory.
 #include "internal.cuh"
@@ -21,14 +21,18 @@ namespace rpca {
 namespace {
 
 constexpr int kJacThreads = 1024;
-constexpr int kLanesPerPair = 4;      // lanes sharing one column pair of a round
 constexpr int kMaxSweeps = 40;
+constexpr float kQuadStop = 5e-4f;    // see the end of a sweep in jacobi_kernel
 
 __host__ __device__ __forceinline__ int even_up(int l) { return l + (l & 1); }
 // row length of the Jacobi CTA's copy of M (16-byte rows for float4 access)
 __host__ __device__ __forceinline__ int jac_ldm(int l) { return (l + 3) & ~3; }
 
-__global__ void __launch_bounds__(kJacThreads)
+// LPP lanes per column pair; CACHE > 0: each lane keeps its CACHE float4 of both
+// columns in registers between the inner products and the rotation (ldm / 4 <=
+// LPP * CACHE), so that a round reads shared memory once.
+template <int LPP, int CACHE>
+__global__ void __launch_bounds__(CACHE > 0 ? 512 : kJacThreads)
 jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int *__restrict__ sweeps_out,
               float *__restrict__ sig, int *__restrict__ perm, float *__restrict__ Wk, int lp, int k,
               int kp, DevStatus *__restrict__ st) {
@@ -37,6 +41,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
     const int ldm = jac_ldm(l);        // multiple of 4, columns l..ldm-1 zero
     const int nv = ldm / 4;            // float4 per row
     __shared__ int s_rot;
+    __shared__ int s_mu;               // largest |c| / sqrt(a b) of the sweep (float bits, >= 0)
     __shared__ float s_sig[RPCA_MAX_L];
     const int tid = threadIdx.x;
     const int L = even_up(l);
@@ -48,48 +53,89 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
     }
     __syncthreads();
 
-    const int g = tid / kLanesPerPair, lane = tid % kLanesPerPair;
+    const int g = tid / LPP, lane = tid % LPP;
     const bool live = g < npairs;
     const float tol = 8.0f * sqrtf((float)l) * 0x1p-24f;
     float2 *rlog = rot + g;
     int sweep = 0;
+    bool early = false;
     for (; sweep < kMaxSweeps; ++sweep) {
-        if (tid == 0) s_rot = 0;
+        if (tid == 0) { s_rot = 0; s_mu = 0; }
         __syncthreads();
         // circle-method round robin: positions g and L-1-g; each step moves every
         // player but 0 one place along 1..L-1
         int pa = g == 0 ? 0 : g, pb = L - 1 - g;
+        float mu_max = 0.f;
         for (int step = 0; step < L - 1; ++step) {
             const int p = live ? min(pa, pb) : 0, q = live ? max(pa, pb) : 0;
             const bool valid = live && q < l;
-            float a = 0.f, b = 0.f, c = 0.f;
+            float a0 = 0.f, b0 = 0.f, c0 = 0.f, a1 = 0.f, b1 = 0.f, c1 = 0.f;
             float4 *mp = Ms4 + p * nv, *mq = Ms4 + q * nv;
-            if (valid) {
-                for (int e = lane; e < nv; e += kLanesPerPair) {
-                    const float4 x = mp[e], y = mq[e];
+            float4 xc[CACHE > 0 ? CACHE : 1], yc[CACHE > 0 ? CACHE : 1];
+            if (CACHE > 0) {
+#pragma unroll
+                for (int it = 0; it < CACHE; ++it) {
+                    const int e = lane + LPP * it;
+                    xc[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    yc[it] = xc[it];
+                    if (valid && e < nv) { xc[it] = mp[e]; yc[it] = mq[e]; }
+                }
+#pragma unroll
+                for (int it = 0; it < CACHE; ++it) {
+                    const float4 x = xc[it], y = yc[it];
+                    float &a = (it & 1) ? a1 : a0, &b = (it & 1) ? b1 : b0, &c = (it & 1) ? c1 : c0;
                     a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
                     b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
                     c = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, c))));
                 }
+            } else if (valid) {
+#pragma unroll 2
+                for (int e = lane; e < nv; e += LPP) {
+                    const float4 x = mp[e], y = mq[e];
+                    a0 = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a0))));
+                    b0 = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b0))));
+                    c0 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, c0))));
+                }
             }
+            float a = a0 + a1, b = b0 + b1, c = c0 + c1;
 #pragma unroll
-            for (int off = 1; off < kLanesPerPair; off <<= 1) {
+            for (int off = 1; off < LPP; off <<= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, off);
                 b += __shfl_xor_sync(0xffffffffu, b, off);
                 c += __shfl_xor_sync(0xffffffffu, c, off);
             }
+            // the rotation that zeroes c (Rutishauser's formulas); only its
+            // orthogonality matters, so the angle is computed with fast intrinsics:
+            // cs^2 + sn^2 = 1 to rounding whatever the error in t
             float cs = 1.f, sn = 0.f;
-            if (valid && fabsf(c) > tol * sqrtf(a * b) && c != 0.f) {
-                const float zeta = (b - a) / (2.f * c);
-                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(zeta, 1.f));
+            const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
+            if (mu > tol) {
+                mu_max = fmaxf(mu_max, mu);
+                const float zeta = __fdividef(b - a, 2.f * c);
+                const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
                 cs = rsqrtf(fmaf(t, t, 1.f));
                 sn = cs * t;
-                for (int e = lane; e < nv; e += kLanesPerPair) {
-                    const float4 x = mp[e], y = mq[e];
-                    mp[e] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
-                                        cs * x.w - sn * y.w);
-                    mq[e] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
-                                        sn * x.w + cs * y.w);
+                if (CACHE > 0) {
+#pragma unroll
+                    for (int it = 0; it < CACHE; ++it) {
+                        const int e = lane + LPP * it;
+                        const float4 x = xc[it], y = yc[it];
+                        if (e < nv) {
+                            mp[e] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
+                                                cs * x.w - sn * y.w);
+                            mq[e] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
+                                                sn * x.w + cs * y.w);
+                        }
+                    }
+                } else {
+#pragma unroll 2
+                    for (int e = lane; e < nv; e += LPP) {
+                        const float4 x = mp[e], y = mq[e];
+                        mp[e] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z,
+                                            cs * x.w - sn * y.w);
+                        mq[e] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z,
+                                            sn * x.w + cs * y.w);
+                    }
                 }
                 s_rot = 1;                       // any rotation this sweep (a flag, not a count)
             }
@@ -99,24 +145,33 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
             pb = pb == 0 ? 0 : (pb == L - 1 ? 1 : pb + 1);
             __syncthreads();
         }
+        // the sweep's largest measure (once per sweep: warp max, one atomic per warp)
+#pragma unroll
+        for (int off = 16; off; off >>= 1) mu_max = fmaxf(mu_max, __shfl_xor_sync(0xffffffffu, mu_max, off));
+        if ((tid & 31) == 0 && mu_max > 0.f) atomicMax(&s_mu, __float_as_int(mu_max));
+        __syncthreads();
         if (s_rot == 0) { ++sweep; break; }
+        // quadratic convergence: after a sweep whose rotations all had measure below
+        // kQuadStop the next sweep's measures are below tol, so it is not run
+        if (__int_as_float(s_mu) < kQuadStop) { ++sweep; early = true; break; }
         __syncthreads();
     }
-    // sweep = number of logged sweeps (the last one made no rotation, or the cap was hit)
+    // sweep = number of logged sweeps (the last one made no rotation or only rotations
+    // below kQuadStop, or the cap was hit)
     if (tid == 0) {
         *sweeps_out = sweep;
         st->jacobi_sweeps = sweep;
-        if (sweep >= kMaxSweeps && s_rot != 0) atomicAdd(&st->jacobi_unconverged, 1);
+        if (sweep >= kMaxSweeps && s_rot != 0 && !early) atomicAdd(&st->jacobi_unconverged, 1);
     }
 
     // singular values = column norms; sort descending (ties by index)
     // (warp-uniform trip count: every lane reaches the full-mask shuffles)
-    for (int j0 = 0; j0 < l; j0 += (int)blockDim.x / kLanesPerPair) {
+    for (int j0 = 0; j0 < l; j0 += (int)blockDim.x / LPP) {
         const int j = j0 + g;
         float s2 = 0.f;
         if (j < l)
-            for (int e = lane; e < l; e += kLanesPerPair) s2 = fmaf(Ms[j * ldm + e], Ms[j * ldm + e], s2);
-        for (int off = 1; off < kLanesPerPair; off <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            for (int e = lane; e < l; e += LPP) s2 = fmaf(Ms[j * ldm + e], Ms[j * ldm + e], s2);
+        for (int off = 1; off < LPP; off <<= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
         if (j < l && lane == 0) s_sig[j] = sqrtf(s2);
     }
     __syncthreads();
@@ -256,13 +311,18 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
                      float *rot, float *zbuf, int *perm, DevStatus *st, cudaStream_t s) {
     int *sweeps = reinterpret_cast<int *>(zbuf);
     const size_t smem = (size_t)l * jac_ldm(l) * sizeof(float);
-    cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)RPCA_MAX_L * jac_ldm(RPCA_MAX_L) * sizeof(float)));
-    // kLanesPerPair lanes per column pair of a round; no idle warps at the round barriers
-    const int threads = (int)std::min<int64_t>(
-        kJacThreads, std::max<int64_t>(64, round_up(kLanesPerPair * (even_up(l) / 2), 32)));
-    jacobi_kernel<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig,
-                                           perm, Wk, lp, k, kp, st);
+    const int smem_max = (int)((size_t)RPCA_MAX_L * jac_ldm(RPCA_MAX_L) * sizeof(float));
+    // l <= 128 (at most 32 float4 per column): four lanes per pair with eight float4
+    // of each column in registers; wider: eight lanes per pair, columns re-read
+    const bool cached = jac_ldm(l) / 4 <= 4 * 8;
+    auto kern = cached ? jacobi_kernel<4, 8> : jacobi_kernel<8, 0>;
+    const int lpp = cached ? 4 : 8;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
+        return RPCA_ERR_CUDA;
+    // lpp lanes per column pair of a round; no idle warps at the round barriers
+    const int threads = (int)std::min<int64_t>(cached ? 512 : kJacThreads,
+                                               std::max<int64_t>(64, round_up(lpp * (even_up(l) / 2), 32)));
+    kern<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig, perm, Wk, lp, k, kp, st);
     RPCA_CHECK_LAUNCH();
     const int grid = (int)cdiv(lp, kReplayWarps);
     replay_kernel<<<grid, kReplayWarps * 32, 0, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
