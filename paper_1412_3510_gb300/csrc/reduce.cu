@@ -34,22 +34,29 @@ colsum_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld, float *__r
         }
     }
     if (!part) return;
-    // threads: column c = t % cw, row group g = t / cw
-    const int cw = min(l, 256);
-    const int groups = 256 / cw;
-    for (int cb = 0; cb < l; cb += cw) {
-        const int t = threadIdx.x;
-        const int c = cb + t % cw;
-        const int g = t / cw;
-        float s = 0.f;
-        if (g < groups && c < l)
-            for (int64_t r = r0 + g; r < r1; r += groups) s += Y[r * ld + c];
-        red[t] = s;
+    // 32 consecutive columns (coalesced rows) x 8 row groups, four independent sums
+    // per thread; the eight group sums are combined in order
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int cb = 0; cb < l; cb += 32) {
+        const int c = cb + tx;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (c < l) {
+            int64_t r = r0 + ty;
+            for (; r + 24 < r1; r += 32) {
+                s0 += Y[r * ld + c];
+                s1 += Y[(r + 8) * ld + c];
+                s2 += Y[(r + 16) * ld + c];
+                s3 += Y[(r + 24) * ld + c];
+            }
+            for (; r < r1; r += 8) s0 += Y[r * ld + c];
+        }
+        red[threadIdx.x] = (s0 + s1) + (s2 + s3);
         __syncthreads();
-        if (t < cw && cb + t < l) {
+        if (ty == 0 && c < l) {
             float tot = 0.f;
-            for (int q = 0; q < groups; ++q) tot += red[q * cw + t];
-            part[(int64_t)blockIdx.x * l + cb + t] = tot;
+            for (int q = 0; q < 8; ++q) tot += red[q * 32 + tx];
+            part[(int64_t)blockIdx.x * l + c] = tot;
         }
         __syncthreads();
     }

@@ -201,32 +201,54 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
 
 // Z = product of the logged rotations applied to the identity.  Every row of Z
 // evolves independently, so each warp owns one row (in shared memory) and applies
-// the rounds in order, lanes taking the disjoint pairs of a round; the CTA stages
-// the logged rotations through shared memory kReplayChunk rounds at a time.
+// the rounds in order, lanes taking the disjoint pairs of a round.  The logged
+// rotations pass through shared memory kReplayChunk rounds at a time, double
+// buffered: the next chunk's loads are in flight while the current one is applied.
 // Zk[i][r] = Z[i][perm[r]].
 constexpr int kReplayWarps = 8;
-constexpr int kReplayChunk = 16;
+constexpr int kReplayChunk = 32;
 constexpr int kReplayGroups = (RPCA_MAX_L / 2 + 31) / 32;   // pair groups per lane
+constexpr int kReplayPre = (kReplayChunk * (RPCA_MAX_L / 2) + kReplayWarps * 32 - 1) / (kReplayWarps * 32);
 
 __global__ void __launch_bounds__(kReplayWarps * 32)
 replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr, int l,
               const int *__restrict__ perm, float *__restrict__ Zk, int lp, int k, int kp) {
     __shared__ float Z[kReplayWarps][RPCA_MAX_L + 1];
-    __shared__ float2 rs[kReplayChunk][RPCA_MAX_L / 2];
+    extern __shared__ float2 rs[];                            // [2][kReplayChunk][npairs]
     const int L = even_up(l), npairs = L / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int i = blockIdx.x * kReplayWarps + warp;           // this warp's row of Z
     for (int c = lane; c < l; c += 32) Z[warp][c] = (i == c) ? 1.f : 0.f;
     const int rounds = *sweeps_ptr * (L - 1);
+    const int nchunks = (rounds + kReplayChunk - 1) / kReplayChunk;
+    float2 pre[kReplayPre];
+    auto load = [&](int ch) {
+        const int c0 = ch * kReplayChunk, n = min(kReplayChunk, rounds - c0) * npairs;
+#pragma unroll
+        for (int u = 0; u < kReplayPre; ++u) {
+            const int e = tid + u * nt;
+            pre[u] = e < n ? rot[(size_t)c0 * npairs + e] : make_float2(1.f, 0.f);
+        }
+    };
+    auto store = [&](int ch) {
+        const int c0 = ch * kReplayChunk, n = min(kReplayChunk, rounds - c0) * npairs;
+        float2 *dst = rs + (size_t)(ch & 1) * kReplayChunk * npairs;
+#pragma unroll
+        for (int u = 0; u < kReplayPre; ++u) {
+            const int e = tid + u * nt;
+            if (e < n) dst[e] = pre[u];
+        }
+    };
+    if (nchunks > 0) { load(0); store(0); }
+    __syncthreads();
     // positions of this lane's pair groups g = lane + 32 u in the round-robin circle
     int pa[kReplayGroups], pb[kReplayGroups];
     int step = 0;
-    for (int c0 = 0; c0 < rounds; c0 += kReplayChunk) {
-        const int nr = min(kReplayChunk, rounds - c0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < nr * npairs; e += blockDim.x)
-            rs[e / npairs][e % npairs] = rot[(size_t)c0 * npairs + e];
-        __syncthreads();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        if (ch + 1 < nchunks) load(ch + 1);
+        const int nr = min(kReplayChunk, rounds - ch * kReplayChunk);
+        const float2 *cur = rs + (size_t)(ch & 1) * kReplayChunk * npairs;
         if (i < l) {
             for (int r = 0; r < nr; ++r, ++step) {
                 if (step == L - 1) step = 0;
@@ -243,7 +265,7 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
                     const int g = lane + 32 * u;
                     const int p = min(pa[u], pb[u]), q = max(pa[u], pb[u]);
                     if (g < npairs && q < l) {
-                        const float2 csn = rs[r][g];
+                        const float2 csn = cur[r * npairs + g];
                         const float x = Z[warp][p], y = Z[warp][q];
                         Z[warp][p] = csn.x * x - csn.y * y;
                         Z[warp][q] = csn.y * x + csn.x * y;
@@ -254,6 +276,8 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
                 __syncwarp();
             }
         }
+        if (ch + 1 < nchunks) store(ch + 1);
+        __syncthreads();
     }
     if (i < lp)
         for (int r = lane; r < kp; r += 32) {
@@ -325,8 +349,12 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
     kern<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig, perm, Wk, lp, k, kp, st);
     RPCA_CHECK_LAUNCH();
     const int grid = (int)cdiv(lp, kReplayWarps);
-    replay_kernel<<<grid, kReplayWarps * 32, 0, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
-                                                     lp, k, kp);
+    const size_t rsmem = (size_t)2 * kReplayChunk * (even_up(l) / 2) * sizeof(float2);
+    if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)2 * kReplayChunk * (RPCA_MAX_L / 2) * sizeof(float2))) != cudaSuccess)
+        return RPCA_ERR_CUDA;
+    replay_kernel<<<grid, kReplayWarps * 32, rsmem, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
+                                                         lp, k, kp);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
