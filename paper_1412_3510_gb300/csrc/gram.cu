@@ -99,9 +99,10 @@ int gram_groups(int lp) {
 }  // namespace
 
 int gram_splits(int64_t rows, int lp) {
-    // partials = CTAs x row groups
+    // partials = CTAs x row groups; short blocks: one 64-row stage per CTA, so that
+    // the few thousand rows of an n-side block still spread over many SMs
     const int rg = gram_groups(lp);
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(cdiv(rows, 256), 4LL * num_sms()));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(cdiv(rows, kRowsStage), 4LL * num_sms()));
     return (int)(blocks * rg);
 }
 
