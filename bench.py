@@ -210,6 +210,27 @@ def traffic_from_profiles(kernel_key, sha):
     return None
 
 
+def capture_graph(rp, step):
+    """One step captured as a CUDA graph on a side stream: (graph, library launches per
+    step), or (None, None) when capture is not possible (the caller then times eager
+    launches).  A warm-up call must have run, so that every kernel attribute and tensor
+    map encoder the step uses is initialised outside the capture."""
+    import torch
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        l0 = rp.rpca_launch_count()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        return g, rp.rpca_launch_count() - l0
+    except Exception as e:                      # noqa: BLE001 - report and time eagerly
+        print(f"CUDA graph capture failed ({e}); timing eager launches", file=sys.stderr)
+        torch.cuda.synchronize()
+        return None, None
+
+
 def pipelined_e2e(steps, upload, compute, download, barrier):
     """End-to-end time per step with two buffer sets: step i uploads its input into set
     i % 2 on a copy stream while step i - 1 computes; every step's upload and read-back
@@ -634,6 +655,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the plain-FP32 and accuracy-bar side runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="dense/CSR: time eager launches instead of a CUDA graph")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--resid-iters", type=int, default=20)
     ap.add_argument("--ref-rows", type=int, default=50000)
@@ -718,11 +740,32 @@ def main():
             sk1 = sigma_k1_secular(sigma, w["colsum"], m, k)
             sk1_how = "secular equation of diag(sigma^2) - z z^T, z = sigma U^T 1 / sqrt(m) (construction)"
 
+    # one PCA captured as a CUDA graph (the library's launches are stream-ordered and
+    # host-synchronisation free); the stage-timing events are captured with it, so each
+    # replay re-records them and the read-out after the timed region is the last step's
+    rp.rpca_timing_reset()
+    rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) + 64)
+    graph, per_step_launches = None, None
+    if not args.no_graph:
+        graph, per_step_launches = capture_graph(rp, step)
+    timing_per_step = graph is not None
+    if not timing_per_step:
+        rp.rpca_timing_reset()
+        rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
+
+    def timed_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+    if graph is not None:
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+
     # timed region
     sampler = ClockSampler(local)
     sampler.start()
-    rp.rpca_timing_reset()
-    rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
     launches0 = rp.rpca_launch_count()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -730,11 +773,13 @@ def main():
     sampler.mark("t0")
     ev0.record(stream)
     for _ in range(args.steps):
-        step()
+        timed_step()
     ev1.record(stream)
     barrier()
     sampler.mark("t1")
     launches = rp.rpca_launch_count() - launches0
+    if graph is not None:
+        launches = per_step_launches * args.steps
     rp.rpca_timing_enable(False)
     sampler.stop()
     ms_total = ev0.elapsed_time(ev1)
@@ -744,12 +789,32 @@ def main():
         ms_total = float(t.item())
     ms_per_step = ms_total / args.steps
     value = world * args.steps / (ms_total / 1e3)
-    n_apply, t_apply = rp.rpca_timing_read(0)
-    n_adj, t_adj = rp.rpca_timing_read(1)
-    n_svd, t_svd = rp.rpca_timing_read(3)
-    extra = {name: rp.rpca_timing_read(kind)[1] / args.steps
-             for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
+    try:
+        n_apply, t_apply = rp.rpca_timing_read(0)
+        n_adj, t_adj = rp.rpca_timing_read(1)
+        n_svd, t_svd = rp.rpca_timing_read(3)
+        timed_steps = 1 if timing_per_step else args.steps      # steps the stage events cover
+        extra = {name: rp.rpca_timing_read(kind)[1] / timed_steps
+                 for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
+    except Exception as e:                                      # noqa: BLE001
+        # the graph's stage events could not be read: time the stages on eager steps
+        print(f"stage events of the graph unreadable ({e}); stage times from eager steps", file=sys.stderr)
+        rp.rpca_timing_reset()
+        rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        rp.rpca_timing_enable(False)
+        timing_per_step = False
+        n_apply, t_apply = rp.rpca_timing_read(0)
+        n_adj, t_adj = rp.rpca_timing_read(1)
+        n_svd, t_svd = rp.rpca_timing_read(3)
+        extra = {name: rp.rpca_timing_read(kind)[1] / args.steps
+                 for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
     rp.rpca_timing_reset()
+    if timing_per_step:
+        n_apply, n_adj = n_apply * args.steps, n_adj * args.steps
+        t_apply, t_adj, t_svd = t_apply * args.steps, t_adj * args.steps, t_svd * args.steps
 
     # roofline of the dominant kernel (the passes over A)
     pk = peaks()
@@ -839,11 +904,14 @@ def main():
                               out=(U, S, V), check=False, renorm=renorm)
             for _ in range(args.warmup):
                 once()
+            g_form = capture_graph(rp, once)[0] if graph is not None else None
+            run_form = g_form.replay if g_form is not None else once
+            run_form()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(side_steps):
-                once()
+                run_form()
             e1.record(stream)
             barrier()
             ms = e0.elapsed_time(e1) / side_steps
@@ -903,7 +971,9 @@ def main():
                                       "products accumulated in FP32 (TMEM); l x l work in FP32"
                                       if args.precision == "bf16x3" else "passes over A in FP32 FFMA"),
                    "A_bytes": int(a_bytes), "l2": "A (%.0f MB) is larger than L2 (129 MB); no flush" % (a_bytes / 1e6),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch": ("one PCA captured as a CUDA graph and replayed per step; stage times from the "
+                              "last replay's events" if graph is not None else "eager launches")},
         "gbs_per_pass": gbs_per_pass,
         "passes_per_step": passes / args.steps,
         "stage_ms_per_step": dict({"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,

@@ -62,14 +62,12 @@ colsum_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld, float *__r
     }
 }
 
-// Y[r][c] -= mean_c (c < l), Y[r][c] = 0 (l <= c < ld); mean from the partials
-// (compensated FP32 sum, recomputed by every CTA).
+// One CTA: the column means (compensated FP32 sums of the partials, in chunk order)
+// overwrite part[0 .. l) once every partial has been read.
 __global__ void __launch_bounds__(256)
-center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
-              const float *__restrict__ part, int nchunks) {
+colmean_kernel(float *__restrict__ part, int64_t rows, int l, int nchunks) {
     __shared__ float mu[RPCA_MAX_L];
-    const int tflat = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int c = tflat; c < l; c += blockDim.x * blockDim.y) {
+    for (int c = threadIdx.x; c < l; c += blockDim.x) {
         float s = 0.f, comp = 0.f;
         for (int q = 0; q < nchunks; ++q) {
             const float y = part[(int64_t)q * l + c] - comp;
@@ -79,6 +77,16 @@ center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld,
         }
         mu[c] = s / (float)rows;
     }
+    __syncthreads();
+    for (int c = threadIdx.x; c < l; c += blockDim.x) part[c] = mu[c];
+}
+
+// Y[r][c] -= mu[c] (c < l), Y[r][c] = 0 (l <= c < ld).
+__global__ void __launch_bounds__(256)
+center_kernel(float *__restrict__ Y, int64_t rows, int l, int64_t ld, const float *__restrict__ mu_g) {
+    __shared__ float mu[RPCA_MAX_L];
+    const int tflat = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int c = tflat; c < l; c += blockDim.x * blockDim.y) mu[c] = mu_g[c];
     __syncthreads();
     // blockDim = (32, 8): threadIdx.x walks the columns of a row, threadIdx.y the rows
     for (int64_t r = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; r < rows; r += (int64_t)gridDim.x * blockDim.y) {
@@ -207,7 +215,9 @@ int launch_finalize(float *Q, int64_t rows, int l, int64_t ld, float ones_value,
 int launch_center(float *Y, int64_t rows, int l, int64_t ld, const float *part, int nchunks,
                   cudaStream_t s) {
     const int64_t grid = std::min<int64_t>(cdiv(rows, 8), (int64_t)num_sms() * 4);
-    center_kernel<<<(unsigned)std::max<int64_t>(grid, 1), dim3(32, 8), 0, s>>>(Y, rows, l, ld, part, nchunks);
+    colmean_kernel<<<1, 256, 0, s>>>(const_cast<float *>(part), rows, l, nchunks);
+    RPCA_CHECK_LAUNCH();
+    center_kernel<<<(unsigned)std::max<int64_t>(grid, 1), dim3(32, 8), 0, s>>>(Y, rows, l, ld, part);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

@@ -25,6 +25,16 @@ cudaEvent_t take_event() {
     return e;
 }
 
+// A stream being captured into a CUDA graph turns a plain event record into a
+// dependency edge; an external record becomes an event node that every replay records.
+void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 }  // namespace
 
 bool timing_on() { return g_on; }
@@ -34,13 +44,13 @@ TimedScope::TimedScope(int kind, cudaStream_t s) : kind_(kind), s_(s) {
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = take_event();
     b_ = take_event();
-    if (a_) cudaEventRecord(a_, s_);
+    if (a_) record(a_, s_);
 }
 
 TimedScope::~TimedScope() {
     if (!a_) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (b_) cudaEventRecord(b_, s_);
+    if (b_) record(b_, s_);
     g_recs.push_back({kind_, a_, b_});
 }
 
