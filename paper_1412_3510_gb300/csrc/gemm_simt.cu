@@ -243,25 +243,25 @@ int choose_splits(int64_t M, int64_t N, int64_t K) {
 
 // C (M x N) = A (M x K) B (K x N) for the small right-hand factors of the
 // pipeline (Y R^-1 with K = N = lp, the lifts Q W and Q2 Z with N = k): B whole in
-// shared memory, a 64-row tile of A, a 16 x 16 thread grid where thread (ty, tx)
-// owns rows ty + 16 i (i < 4) and columns tx + 16 j (j < NG).  copy_flag == 0 makes
-// B the identity (C = A, N == K).
-constexpr int kSkRows = 64;
-
-template <int NG>
+// shared memory, a 16 RPT-row tile of A, a 16 x 16 thread grid where thread (ty, tx)
+// owns rows ty + 16 i (i < RPT) and columns tx + 16 j (j < NG).  RPT = 1 for short
+// blocks (the n side: a few thousand rows spread over many SMs), 4 for long ones.
+// copy_flag == 0 makes B the identity (C = A, N == K).
+template <int NG, int RPT>
 __global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int K, const float *__restrict__ A,
                                                           int64_t lda, const float *__restrict__ B, int64_t ldb,
                                                           float *__restrict__ C, int64_t ldc,
                                                           const int *__restrict__ copy_flag) {
     extern __shared__ float sk[];
     constexpr int NB = 16 * NG;                  // B columns in shared memory
+    constexpr int kRows = 16 * RPT;              // rows of A per CTA
     const int lda_s = K + 1;                     // odd: the 16 row-owners hit 16 banks
     float *Bs = sk;                              // K x NB
-    float *As = sk + (size_t)K * NB;             // kSkRows x lda_s
+    float *As = sk + (size_t)K * NB;             // kRows x lda_s
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * kSkRows;
+    const int64_t m0 = (int64_t)blockIdx.x * kRows;
     if (copy_flag && *copy_flag == 0) {
-        for (int e = tid; e < kSkRows * N; e += 256) {
+        for (int e = tid; e < kRows * N; e += 256) {
             const int64_t r = m0 + e / N;
             const int c = e % N;
             if (r < M) C[r * ldc + c] = A[r * lda + c];
@@ -272,29 +272,29 @@ __global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int 
         const int k = e / NB, c = e - k * NB;
         Bs[e] = c < N ? B[(int64_t)k * ldb + c] : 0.f;
     }
-    for (int e = tid; e < kSkRows * K; e += 256) {
+    for (int e = tid; e < kRows * K; e += 256) {
         const int r = e / K, k = e - r * K;
         As[r * lda_s + k] = m0 + r < M ? A[(m0 + r) * lda + k] : 0.f;
     }
     __syncthreads();
-    float acc[4][NG];
+    float acc[RPT][NG];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int j = 0; j < NG; ++j) acc[i][j] = 0.f;
     for (int k = 0; k < K; ++k) {
-        float a[4], b[NG];
+        float a[RPT], b[NG];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[(ty + 16 * i) * lda_s + k];
+        for (int i = 0; i < RPT; ++i) a[i] = As[(ty + 16 * i) * lda_s + k];
 #pragma unroll
         for (int j = 0; j < NG; ++j) b[j] = Bs[k * NB + tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < RPT; ++i)
 #pragma unroll
             for (int j = 0; j < NG; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RPT; ++i) {
         const int64_t r = m0 + ty + 16 * i;
         if (r >= M) continue;
 #pragma unroll
@@ -308,12 +308,14 @@ __global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int 
 template <int NG>
 int launch_smallk(int64_t M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
                   int64_t ldc, cudaStream_t s, const int *copy_flag) {
-    const size_t smem = ((size_t)K * 16 * NG + (size_t)kSkRows * (K + 1)) * sizeof(float);
-    if (cudaFuncSetAttribute(smallk_gemm_kernel<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    // 64-row tiles while they fill two waves of the SMs, 16-row tiles below that
+    const bool short_block = cdiv(M, (int64_t)64) < 2LL * num_sms();
+    const int rows = short_block ? 16 : 64;
+    const size_t smem = ((size_t)K * 16 * NG + (size_t)rows * (K + 1)) * sizeof(float);
+    auto kern = short_block ? smallk_gemm_kernel<NG, 1> : smallk_gemm_kernel<NG, 4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RPCA_ERR_CUDA;
-    smallk_gemm_kernel<NG><<<(unsigned)cdiv(M, (int64_t)kSkRows), 256, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                                                   copy_flag);
+    kern<<<(unsigned)cdiv(M, (int64_t)rows), 256, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, copy_flag);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
