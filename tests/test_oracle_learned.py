@@ -100,3 +100,30 @@ def test_forward_bf16_close_to_exact():
     # BF16 keeps 8 bits: the outputs agree to a few parts in 1e3 of their scale
     assert np.max(np.abs(y - yb)) < 0.02 * max(1.0, np.max(np.abs(y)))
     assert not np.array_equal(y, yb)
+
+
+def test_weights_from_output_closed_form_and_clip():
+    # d = exp(y) between the clip bounds 1e-2 and 1e2, so the prediction of a
+    # leverage label t = log(n lev / k + 1e-3) maps back to n lev / k + 1e-3
+    y = np.array([0.0, math.log(5.0), math.log(0.25), 10.0, -10.0, math.log(100.0), math.log(0.01)])
+    d = L.weights_from_output(y)
+    assert np.allclose(d, [1.0, 5.0, 0.25, 100.0, 0.01, 100.0, 0.01], rtol=1e-12)
+    ys = np.linspace(-8, 8, 401)
+    ds = L.weights_from_output(ys)
+    assert np.all(np.diff(ds) >= 0) and ds.min() == 0.01 and ds.max() == 100.0
+    n, k = 50, 4
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((n, k)))
+    lev = (Q ** 2).sum(axis=1)
+    assert np.allclose(L.weights_from_output(L.leverage_target(Q, k)),
+                       np.clip(n * lev / k + 1e-3, 1e-2, 1e2), rtol=1e-12)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    # with bias correction, m_hat = g and v_hat = g^2 after one step, so every
+    # coordinate moves by lr g / (|g| + eps), i.e. lr sign(g) for |g| >> eps
+    rng = np.random.default_rng(11)
+    p = rng.standard_normal(40)
+    g = rng.standard_normal(40) * np.logspace(-3, 3, 40)
+    p1, m1, m2 = L.adam_step(p, g, np.zeros(40), np.zeros(40), 1, 1e-3)
+    assert np.allclose(p - p1, 1e-3 * np.sign(g), rtol=1e-4, atol=0)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(m2, 1e-3 * g * g)
