@@ -59,6 +59,9 @@ typedef enum rpca_status {
 /* Largest sketch width l (the l x l factors live in one CTA's shared memory). */
 #define RPCA_MAX_L 224
 
+/* In both forms the renormalisations' tall products (Gram matrices, Y R^-1, the
+ * lift U = Q W) of blocks with >= 16384 rows run on the tensor cores split in three
+ * BF16 pieces (exact) with the six products of order <= 2^-18: FP32 accuracy. */
 typedef enum rpca_precision {
     RPCA_PREC_FP32 = 0,          /* passes over A in FP32 FFMA (the plain form) */
     RPCA_PREC_BF16X3 = 1         /* passes over A on tcgen05 tensor cores: a = a_hi + a_lo
@@ -134,7 +137,8 @@ int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const in
  * max_n       : an upper bound on every descriptor's n.
  * o           : k <= l <= 32 and l <= min(m, n) for every matrix;
  *               n * round_up(l + 1, 8) <= 24576; o->omega must be NULL; o->seed
- *               keys Omega exactly as in rpca_dense; precision is FP32.
+ *               keys Omega exactly as in rpca_dense; precision is FP32;
+ *               renorm is RPCA_RENORM_CHOLQR (else RPCA_ERR_UNSUPPORTED).
  * col_weights : NULL, or a device array of count device pointers, each NULL
  *               or an n-vector d: that matrix's sketch uses diag(d) Omega.
  * item_status : NULL, or count int32 (device): 0 on success, RPCA_ERR_INVALID_ARG
