@@ -57,3 +57,19 @@ def test_argument_errors_need_no_gpu(lib):
     # misaligned or short workspace
     assert L.rpca_dense(fake, 100, 50, 50, ctypes.byref(o), fake, 5, fake, fake, 5, ctypes.c_void_p(257), 1 << 30, None) == _lib.RPCA_ERR_WORKSPACE
     assert L.rpca_dense(fake, 100, 50, 50, ctypes.byref(o), fake, 5, fake, fake, 5, fake, 16, None) == _lib.RPCA_ERR_WORKSPACE
+
+
+def test_option_errors_need_no_gpu(lib):
+    L = _lib.load()
+    fake = ctypes.c_void_p(256)
+    o = _lib.RpcaOpts()
+    L.rpca_default_opts(ctypes.byref(o), 150)
+    o.l = 170
+    o.renorm = 1                      # the LU renormalisation holds 2l x (l + 1) per node: l <= 160
+    args = (fake, 4000, 1000, 1000, ctypes.byref(o), fake, 150, fake, fake, 150, fake, 1 << 40, None)
+    assert L.rpca_dense(*args) == _lib.RPCA_ERR_UNSUPPORTED
+    o.renorm = 2                      # not a renormalisation
+    assert L.rpca_dense(*args) == _lib.RPCA_ERR_INVALID_ARG
+    o.renorm = 0
+    o.precision = 5                   # not a precision
+    assert L.rpca_dense(*args) == _lib.RPCA_ERR_INVALID_ARG
