@@ -210,6 +210,21 @@ def traffic_from_profiles(kernel_key, sha):
     return None
 
 
+def max_over_ranks(x, dist, world, device):
+    """The largest of every rank's x (the slowest rank's time); x itself with one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms):
+    """Whole-job throughput of replicas: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def capture_graph(rp, step):
     """One step captured as a CUDA graph on a side stream: (graph, library launches per
     step), or (None, None) when capture is not possible (the caller then times eager
@@ -782,13 +797,9 @@ def main():
         launches = per_step_launches * args.steps
     rp.rpca_timing_enable(False)
     sampler.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, world, dev)
     ms_per_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
+    value = job_throughput(world, args.steps, ms_total)
     try:
         n_apply, t_apply = rp.rpca_timing_read(0)
         n_adj, t_adj = rp.rpca_timing_read(1)
