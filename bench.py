@@ -673,6 +673,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="dense/CSR: time eager launches instead of a CUDA graph")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--resid-iters", type=int, default=20)
+    ap.add_argument("--resid-iters-conv", type=int, default=60,
+                    help="estimator iterations for the accuracy verdict (converged on the workloads here)")
+    ap.add_argument("--configured-its", action="store_true",
+                    help="time the configured its even when it misses resid <= 1.1 sigma_{k+1}")
     ap.add_argument("--ref-rows", type=int, default=50000)
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--no-learned", action="store_true", help="batched workloads: skip the learned-sketch A/B")
@@ -727,33 +731,55 @@ def main():
     V = torch.empty(n, k, device=dev)
     stream = torch.cuda.current_stream()
 
-    def run(Ain):
+    def run(Ain, its_r):
         if csr:
-            rp.rpca_csr(*Ain, (m, n), k, l, its=its, raw=raw, seed=1 + rank, ws=ws, out=(U, S, V), check=False)
+            rp.rpca_csr(*Ain, (m, n), k, l, its=its_r, raw=raw, seed=1 + rank, ws=ws, out=(U, S, V), check=False)
         else:
-            rp.rpca_dense(Ain, k, l, its=its, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
+            rp.rpca_dense(Ain, k, l, its=its_r, raw=raw, seed=1 + rank, precision=args.precision, ws=ws,
                           out=(U, S, V), check=False)
 
+    def estimate(iters):
+        if csr:
+            return rp.rpca_resid_norm_csr(*A, (m, n), U, S, V, raw=raw, iters=iters, seed=7)
+        return rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=iters, seed=7)
+
+    # sigma_{k+1} of A_c, the metric's accuracy bar resid <= 1.1 sigma_{k+1}
+    if csr:
+        sk1 = sigma_k1_csr(A, (m, n), k)
+        sk1_how = "torch.svd_lowrank (q = k + 30, 30 power iterations)"
+    elif n <= 4096 or raw:
+        sk1 = sigma_k1_reference(A, k, raw)
+        sk1_how = "FP64 Gram of the centred stored matrix, eigvalsh"
+    else:
+        sk1 = sigma_k1_secular(sigma, w["colsum"], m, k)
+        sk1_how = "secular equation of diag(sigma^2) - z z^T, z = sigma U^T 1 / sqrt(m) (construction)"
+
+    # The metric is throughput at resid <= 1.1 sigma_{k+1}.  The residual is judged by the
+    # Section 4 estimator at a converged iteration count (the 20-iteration figure is
+    # reported beside it); when the configured its misses the bar, the headline is the
+    # smallest its that meets it (at most its + 4) and the configured its is a side form.
+    its_cfg = its
+    accuracy_by_its = {}
+    its_h = its_cfg
+    for its_b in range(its_cfg, its_cfg + 5):
+        for _ in range(args.warmup if its_b == its_cfg else 1):
+            run(A, its_b)
+        e20, econv = estimate(args.resid_iters), estimate(args.resid_iters_conv)
+        accuracy_by_its[str(its_b)] = {"resid_over_sigma_k1": econv / sk1, "resid20_over_sigma_k1": e20 / sk1}
+        its_h = its_b
+        if econv <= 1.1 * sk1 or args.configured_its:
+            break
+    its = its_h
+
     def step():
-        run(A)
+        run(A, its)
 
     for _ in range(args.warmup):
         step()
     status = rp.rpca_read_status(ws)
     block = rp.read_status_block(ws)
-
-    # accuracy check outside the timed region: resid <= 1.1 sigma_{k+1}
-    if csr:
-        est = rp.rpca_resid_norm_csr(*A, (m, n), U, S, V, raw=raw, iters=args.resid_iters, seed=7)
-        sk1 = sigma_k1_csr(A, (m, n), k)
-    else:
-        est = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
-        if n <= 4096 or raw:
-            sk1 = sigma_k1_reference(A, k, raw)
-            sk1_how = "FP64 Gram of the centred stored matrix, eigvalsh"
-        else:
-            sk1 = sigma_k1_secular(sigma, w["colsum"], m, k)
-            sk1_how = "secular equation of diag(sigma^2) - z z^T, z = sigma U^T 1 / sqrt(m) (construction)"
+    est20 = estimate(args.resid_iters)
+    est = estimate(args.resid_iters_conv)
 
     # one PCA captured as a CUDA graph (the library's launches are stream-ordered and
     # host-synchronisation free); the stage-timing events are captured with it, so each
@@ -903,8 +929,9 @@ def main():
                "mode": "double-buffered: the upload of step i+1 overlaps step i"}
         del hosts, devs, outs, outs_h
 
-    # side runs (after the timed region): the plain FP32 form on the same workload, and the
-    # smallest its that meets resid <= 1.1 sigma_{k+1} when the configured its does not
+    # side runs (after the timed region), each captured as its own graph: the configured
+    # its when the headline had to raise it, and at the headline's its the plain FP32
+    # form and Section 5's LU renormalisation
     forms = None
     if not args.no_forms and not csr:
         side_steps = max(10, min(args.steps, 50))
@@ -933,25 +960,24 @@ def main():
             return ms
 
         forms = {}
+        if its != its_cfg:
+            ms_c = time_form(args.precision, its_cfg)
+            forms["configured_its"] = {"its": its_cfg, "value": world / (ms_c / 1e3), "ms_per_step": ms_c,
+                                       "precision": args.precision, "steps": side_steps,
+                                       "resid_over_sigma_k1": accuracy_by_its[str(its_cfg)]["resid_over_sigma_k1"],
+                                       "resid_ok": False}
         ms_fp32 = time_form("fp32", its)
-        forms["plain_fp32"] = {"value": world / (ms_fp32 / 1e3), "ms_per_step": ms_fp32, "steps": side_steps,
+        est_fp32 = estimate(args.resid_iters_conv)
+        forms["plain_fp32"] = {"its": its, "value": world / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
+                               "steps": side_steps, "resid_over_sigma_k1": est_fp32 / sk1,
                                "speedup_of_headline": ms_fp32 / ms_per_step}
         if l <= 160 and its > 0:
             # Section 5's LU renormalisation (tall-skinny LU) in place of CholeskyQR
             ms_lu = time_form(args.precision, its, renorm="lu")
-            est_lu = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
-            forms["lu_renorm"] = {"value": world / (ms_lu / 1e3), "ms_per_step": ms_lu, "steps": side_steps,
-                                  "precision": args.precision, "resid_over_sigma_k1": est_lu / sk1,
-                                  "speedup_of_headline": ms_lu / ms_per_step}
-        if est > 1.1 * sk1:
-            for its_b in range(its + 1, its + 4):
-                ms_b = time_form(args.precision, its_b)
-                est_b = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=args.resid_iters, seed=7)
-                forms["at_accuracy_bar"] = {"its": its_b, "value": world / (ms_b / 1e3), "ms_per_step": ms_b,
-                                            "precision": args.precision, "resid_over_sigma_k1": est_b / sk1,
-                                            "steps": side_steps}
-                if est_b <= 1.1 * sk1:
-                    break
+            est_lu = estimate(args.resid_iters_conv)
+            forms["lu_renorm"] = {"its": its, "value": world / (ms_lu / 1e3), "ms_per_step": ms_lu,
+                                  "steps": side_steps, "precision": args.precision,
+                                  "resid_over_sigma_k1": est_lu / sk1, "speedup_of_headline": ms_lu / ms_per_step}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -976,6 +1002,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3" if args.precision == "bf16x3" else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "its": its, "raw": raw,
+                   "its_configured": its_cfg,
+                   "its_note": ("the configured its meets resid <= 1.1 sigma_{k+1}" if its == its_cfg else
+                                f"the configured its={its_cfg} misses resid <= 1.1 sigma_{{k+1}} "
+                                f"(resid/sigma_k1 = {accuracy_by_its[str(its_cfg)]['resid_over_sigma_k1']:.3f}); "
+                                f"the headline is the smallest its that meets it, its={its}"),
                    "format": "csr" if csr else "dense", "nnz": w.get("nnz"),
                    "precision": args.precision, "renorm": "cholqr",
                    "precision_note": ("passes over A: A and the block split into BF16 hi + lo, three tcgen05 "
@@ -989,8 +1020,9 @@ def main():
         "passes_per_step": passes / args.steps,
         "stage_ms_per_step": dict({"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,
                                    "small_svd": t_svd / args.steps}, **extra),
-        "accuracy": {"resid_est": est, "sigma_k1": sk1, "sigma_k1_from": sk1_how if not csr else "torch.svd_lowrank",
-                     "resid_over_sigma_k1": est / sk1,
+        "accuracy": {"resid_est": est, "resid_est_iters": args.resid_iters_conv, "sigma_k1": sk1,
+                     "sigma_k1_from": sk1_how, "resid_over_sigma_k1": est / sk1,
+                     "resid20_over_sigma_k1": est20 / sk1, "by_its": accuracy_by_its,
                      "resid_ok": bool(est <= 1.1 * sk1), "status": status, "shifts": block["shifts"],
                      "jacobi_sweeps": block["jacobi_sweeps"]},
         "clocks": sampler.summary(),

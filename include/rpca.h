@@ -222,9 +222,10 @@ int rpca_dense_pass(const float *A, int64_t m, int64_t n, int64_t lda, int32_t a
  * device that loads the library holds until the process exits.
  *  - Problems whose rpca_dense_pass_workspace_size exceeds that size are
  *    rejected with RPCA_ERR_WORKSPACE before anything runs.
- *  - The first call on a device looks up the buffer's device address (once
- *    per device, with that device current); make that first call before any
- *    CUDA stream capture.
+ *  - Every call looks up the buffer's device address on the current device
+ *    (a host-side query, nothing is allocated).  The first call on a device
+ *    also loads the library's device code there if nothing else has; make
+ *    that first call before any CUDA stream capture.
  *  - All calls share the one buffer and it keeps the previous call's
  *    contents; each call clears the status word it needs on `stream` first.
  *    Calls whose work overlaps on the GPU (other streams, other host threads)

@@ -12,31 +12,22 @@
 // from g_pass_scratch below.
 #include "internal.cuh"
 
-#include <mutex>
-
 // One buffer per device, created when the library's device code is loaded on
 // that device and held until the process exits.
 static __device__ __align__(256) unsigned char g_pass_scratch[RPCA_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
 // Device address of g_pass_scratch on the current device.  Host code cannot
-// use the symbol itself (on the host it names a stand-in, not device memory),
-// so the address is looked up once per device and cached.
+// use the symbol itself (on the host it names a stand-in, not device memory).
+// The address is looked up on every call rather than cached: the lookup is a
+// host-side table query, and a cached address would go stale if the caller's
+// framework reset the device's primary context (the module, and with it the
+// buffer, is then loaded again at another address).
 int scratch_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RPCA_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_pass_scratch) != cudaSuccess || !p) return RPCA_ERR_CUDA;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pass_scratch) != cudaSuccess || !p) return RPCA_ERR_CUDA;
+    *out = p;
     return RPCA_OK;
 }
 

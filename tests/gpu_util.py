@@ -40,3 +40,35 @@ def subspace_tol(s_ref, k, rel_pert=3e-5):
         return 0, 0.0
     gap = max(s_ref[kk - 1] - s_ref[kk], 1e-300)
     return kk, max(1e-3, rel_pert * s_ref[0] / gap)
+
+
+def exact_resid_device(A, U, S, V, raw):
+    """||A_c - U diag(S) V^T||_2 of a device matrix, from the FP64 Gram of the residual
+    (torch eigvalsh on the device; measurement only).  Squaring costs u_64 (s_1/s)^2 of
+    relative accuracy, far below the 1e-3 bars it is used with."""
+    import torch
+    m, n = A.shape
+    Ud, Sd, Vd = U.double(), S.double(), V.double()
+    mean = None if raw else A.double().mean(0)
+    G = torch.zeros(n, n, dtype=torch.float64, device=A.device)
+    for i in range(0, m, 8192):
+        blk = A[i:i + 8192].double()
+        if mean is not None:
+            blk = blk - mean
+        blk = blk - (Ud[i:i + 8192] * Sd) @ Vd.T
+        G.addmm_(blk.T, blk)
+    return float(torch.linalg.eigvalsh(G)[-1].clamp_min(0).sqrt().item())
+
+
+def exact_singular_values_device(A, raw):
+    """All singular values of A_c (descending) from the FP64 Gram on the device (measurement only)."""
+    import torch
+    m, n = A.shape
+    mean = None if raw else A.double().mean(0)
+    G = torch.zeros(n, n, dtype=torch.float64, device=A.device)
+    for i in range(0, m, 8192):
+        blk = A[i:i + 8192].double()
+        if mean is not None:
+            blk = blk - mean
+        G.addmm_(blk.T, blk)
+    return torch.linalg.eigvalsh(G).flip(0).clamp_min(0).sqrt().cpu().numpy()

@@ -55,6 +55,28 @@ def test_features_closed_forms():
     assert np.all(F[:, 13:] == 0)
 
 
+def test_peak_ratio_feature_closed_forms():
+    """f2 = log(m max|a'|^2 / |a'|^2) / 4 of a column: a single spike carries all its
+    energy in one entry (log(m) / 4), a column of equal magnitudes none (0), and a
+    column with p equal nonzeros gives log(m / p) / 4."""
+    m, n = 256, 6
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((m, n))
+    A[:, 0] = 0.0
+    A[17, 0] = -2.5                                   # one spike
+    A[:, 1] = np.where(rng.random(m) < 0.5, 1.0, -1.0)   # +-1
+    A[:, 2] = 0.0
+    A[:32, 2] = 3.0                                   # 32 equal nonzeros
+    F = L.features(A, raw=True, seed=2)
+    assert np.isclose(F[0, 2], math.log(m) / 4, atol=1e-9)
+    assert np.isclose(F[1, 2], 0.0, atol=1e-9)
+    assert np.isclose(F[2, 2], math.log(m / 32) / 4, atol=1e-9)
+    # centred: a balanced +-1 column has mean 0, so it is unchanged by the centring
+    B = A.copy()
+    B[:, 1] = np.tile([1.0, -1.0], m // 2)
+    assert np.isclose(L.features(B, raw=False, seed=2)[1, 2], 0.0, atol=1e-9)
+
+
 def test_leverage_target_on_known_vectors():
     n, k = 50, 4
     V = np.zeros((n, k))
