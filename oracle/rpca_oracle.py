@@ -22,6 +22,13 @@ Sections and equations cited:
   applied as (Q'*A)'.
 * Section 4 (Measuring accuracy): the spectral norm of A - U Sigma V^*
   estimated by the power method from a random start.
+* Section 5, self-adjoint A: the printed loop Q = A*Q with LU on all but the
+  last iteration and QR on the last (``self_adjoint_range``, ``rpca_sym``);
+  the last paragraph's renormalisation in odd-numbered iterations only
+  (``odd_only``).
+* Section 3 (Stabilizing the Nystrom method): B1 = A Q, B2 = Q^* B1,
+  C^* C = B2, F = B1 C^-1, U S V^* = F, Sigma = S^2, stabilised by adding a
+  multiple of the identity and subtracting it again (``nystrom``).
 
 The Gaussian test matrix is drawn from Philox4x64-10 (Salmon, Moraes, Dror &
 Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) with the
@@ -43,6 +50,7 @@ __all__ = [
     "philox4x64_10", "uniform23", "gaussian_omega", "column_means",
     "apply_centred", "apply_centred_adjoint", "lu_renorm", "householder_qr",
     "jacobi_svd", "round_robin_steps", "normalise_signs", "rpca",
+    "self_adjoint_range", "rpca_sym", "cholesky_upper", "nystrom_shift", "nystrom",
     "resid_power", "resid_exact", "exact_singular_values",
 ]
 
@@ -338,7 +346,8 @@ def normalise_signs(U: np.ndarray, V: np.ndarray):
 # ---------------------------------------------------------------------------
 
 def rpca(A, k: int, l: int | None = None, its: int = 2, raw: bool = False,
-         seed: int = 0, omega: np.ndarray | None = None):
+         seed: int = 0, omega: np.ndarray | None = None, odd_only: bool = False,
+         trace: list | None = None):
     """Rank-k approximation A_c ~ U diag(S) V^T by the randomized method.
 
     A: m x n (any real dtype; widened to FP64).  l defaults to k + 2 and its
@@ -353,6 +362,15 @@ def rpca(A, k: int, l: int | None = None, its: int = 2, raw: bool = False,
     4. W Sigma V^* = B by one-sided Jacobi (Eq. i3); U = Q W (Eq. i4).
     5. Keep the leading k triplets; fix signs as in ``normalise_signs``.
     Returns (U m x k, S k, V n x k), all FP64.
+
+    odd_only: Section 5's last optimisation, renormalising only after the
+    odd-numbered applications.  The products are numbered in the order they
+    are applied (the sketch is the first, then A^* and A alternate), as the
+    self-adjoint loop of Section 5 numbers its one product per iteration; so
+    the LU after every product with A^* is dropped and the pair A_c (A_c^* Q)
+    is applied unrenormalised.  The final QR is kept.
+    trace: when a list is given, the steps are appended to it by name
+    ("A", "A*", "lu", "qr"), for checking the control flow.
     """
     A = _as_f64(A)
     m, n = A.shape
@@ -360,22 +378,168 @@ def rpca(A, k: int, l: int | None = None, its: int = 2, raw: bool = False,
         l = k + 2
     if not (1 <= k <= l <= min(m, n)) or its < 0:
         raise ValueError("need 1 <= k <= l <= min(m, n) and its >= 0")
+    log = trace.append if trace is not None else (lambda _s: None)
     c = None if raw else column_means(A)
     Om = gaussian_omega(n, l, seed) if omega is None else np.asarray(omega, dtype=np.float64)
     Y = apply_centred(A, Om, c)
+    log("A")
     if its == 0:
         Q, _ = householder_qr(Y)
+        log("qr")
     else:
         Q, _ = lu_renorm(Y)
+        log("lu")
         for it in range(1, its + 1):
-            Q, _ = lu_renorm(apply_centred_adjoint(A, Q, c))
+            Q = apply_centred_adjoint(A, Q, c)
+            log("A*")
+            if not odd_only:
+                Q, _ = lu_renorm(Q)
+                log("lu")
             Y = apply_centred(A, Q, c)
+            log("A")
             Q, _ = lu_renorm(Y) if it < its else householder_qr(Y)
+            log("lu" if it < its else "qr")
     Bt = apply_centred_adjoint(A, Q, c)      # n x l, = B^*
+    log("A*")
     W, s, V = jacobi_svd(Bt.T)               # B = W diag(s) V^T
     U = Q @ W[:, :k]
     U, V = normalise_signs(U, V[:, :k])
     return U, s[:k].copy(), V
+
+
+# ---------------------------------------------------------------------------
+# self-adjoint A (Section 5's loop) and the stabilised Nystrom method (Section 3)
+# ---------------------------------------------------------------------------
+
+def self_adjoint_range(A, l: int, its: int, seed: int = 0, omega: np.ndarray | None = None,
+                       odd_only: bool = False, trace: list | None = None) -> np.ndarray:
+    """Section 5's core iterations for a self-adjoint n x n A, as printed there.
+
+    Q starts as the n x l random matrix (Section 2).  For it = 1..its:
+    Q = A Q; then Q = lu(Q) when it < its, and Q = qr(Q) when it == its.
+    With odd_only (Section 5's last paragraph) the LU runs only when it is odd.
+    Returns the n x l orthonormal Q.  Needs its >= 1 (with none, Q would be the
+    random matrix itself).
+    """
+    A = _as_f64(A)
+    n = A.shape[0]
+    if A.shape[1] != n or its < 1 or not (1 <= l <= n):
+        raise ValueError("need a square A, its >= 1 and 1 <= l <= n")
+    log = trace.append if trace is not None else (lambda _s: None)
+    Q = gaussian_omega(n, l, seed) if omega is None else np.asarray(omega, dtype=np.float64)
+    for it in range(1, its + 1):
+        Q = np.asarray(A @ Q)
+        log("A")
+        if it < its and (not odd_only or it % 2 == 1):
+            Q, _ = lu_renorm(Q)
+            log("lu")
+        if it == its:
+            Q, _ = householder_qr(Q)
+            log("qr")
+    return Q
+
+
+def rpca_sym(A, k: int, l: int | None = None, its: int = 2, seed: int = 0,
+             omega: np.ndarray | None = None, odd_only: bool = False, trace: list | None = None):
+    """Rank-k approximation of a self-adjoint A (n x n): A ~ U diag(S) V^T with
+    V = U diag(sign(lambda)), i.e. A ~ U diag(lambda) U^T.
+
+    1. Q from ``self_adjoint_range`` (only products with A: A^* = A).
+    2. B = Q^* A Q (l x l), symmetrised as (B + B^T) / 2 (the projection of
+       Eq. i2 taken on both sides, which keeps the approximation self-adjoint).
+    3. B = W diag(s) J^T by one-sided Jacobi (Eq. i3); for symmetric B,
+       J_j = sign(lambda_j) W_j, so lambda_j = s_j sign(W_j . J_j).
+    4. U = Q W, V = Q J (Eq. i4), leading k; signs as in ``normalise_signs``.
+    The column centring of Section 5 does not apply: the centred matrix of a
+    self-adjoint A is not self-adjoint.  Returns (U, S, V), FP64.
+    """
+    A = _as_f64(A)
+    n = A.shape[0]
+    if l is None:
+        l = k + 2
+    if not (1 <= k <= l <= n):
+        raise ValueError("need 1 <= k <= l <= n")
+    log = trace.append if trace is not None else (lambda _s: None)
+    Q = self_adjoint_range(A, l, its, seed, omega, odd_only, trace)
+    Z = np.asarray(A @ Q)
+    log("A")
+    B = Q.T @ Z
+    B = 0.5 * (B + B.T)
+    W, s, J = jacobi_svd(B)
+    U, V = normalise_signs(Q @ W[:, :k], Q @ J[:, :k])
+    return U, s[:k].copy(), V
+
+
+def cholesky_upper(B: np.ndarray) -> np.ndarray:
+    """Upper-triangular C with C^T C = B for a symmetric positive-definite B (the
+    textbook column-by-column Cholesky): C_jj = sqrt(B_jj - sum_{t<j} C_tj^2),
+    C_ji = (B_ji - sum_{t<j} C_tj C_ti) / C_jj for i > j."""
+    B = np.asarray(B, dtype=np.float64)
+    l = B.shape[0]
+    C = np.zeros_like(B)
+    for j in range(l):
+        d = B[j, j] - C[:j, j] @ C[:j, j]
+        if not d > 0.0:
+            raise np.linalg.LinAlgError("matrix is not positive definite")
+        C[j, j] = math.sqrt(d)
+        C[j, j + 1:] = (B[j, j + 1:] - C[:j, j] @ C[:j, j + 1:]) / C[j, j]
+    return C
+
+
+# Unit roundoff of the FP32 arithmetic the shift of the Nystrom method is scaled by.
+NYSTROM_U = 2.0 ** -24
+
+
+def nystrom_shift(B2: np.ndarray, n: int) -> float:
+    """The multiple nu of the identity added to A (and subtracted from the result).
+
+    Section 3 leaves its size open ("an appropriate multiple"); the reading
+    taken is nu = sqrt(n) u tr(B2) with u = 2^-24: the FP32 rounding of the
+    n-term products that form B2 = Q^* A Q is about sqrt(n) u |A| per entry,
+    and tr(B2) bounds |B2|, so B2 + nu I stays positive definite.
+    """
+    return math.sqrt(n) * NYSTROM_U * float(np.trace(B2))
+
+
+def nystrom(A, k: int, l: int | None = None, its: int = 2, seed: int = 0,
+            omega: np.ndarray | None = None, odd_only: bool = False):
+    """Stabilised Nystrom approximation A ~ U diag(S) U^T of a self-adjoint,
+    nonnegative-definite A (n x n), Section 3 with the identity shift.
+
+    Q: the orthonormal n x l basis of ``self_adjoint_range``.  Then, for
+    A + nu I (nu from ``nystrom_shift`` of Q^* A Q):
+      B1 = A Q + nu Q                  (eq. start)
+      B2 = Q^* B1, symmetrised         (eq. second)
+      C^* C = B2, C upper triangular   (eq. Cholesky)
+      F = B1 C^-1                      (eq. pseudo, by triangular solves)
+      U S V^* = F                      (one-sided Jacobi on F)
+      Sigma = S^2 - nu, clipped at 0   (eq. finish, the shift subtracted)
+    Returns (U n x k, Sigma k), leading k, each U column's largest-|entry|
+    positive, FP64.
+    """
+    A = _as_f64(A)
+    n = A.shape[0]
+    if l is None:
+        l = k + 2
+    if not (1 <= k <= l <= n):
+        raise ValueError("need 1 <= k <= l <= n")
+    Q = self_adjoint_range(A, l, its, seed, omega, odd_only)
+    AQ = np.asarray(A @ Q)
+    B2 = Q.T @ AQ
+    nu = nystrom_shift(0.5 * (B2 + B2.T), n)
+    B1 = AQ + nu * Q
+    B2 = Q.T @ B1
+    B2 = 0.5 * (B2 + B2.T)
+    C = cholesky_upper(B2)                  # C^* C = B2, C upper triangular
+    # F C = B1 by forward substitution on the columns of F (C upper triangular)
+    F = np.zeros_like(B1)
+    for j in range(l):
+        F[:, j] = (B1[:, j] - F[:, :j] @ C[:j, j]) / C[j, j]
+    Uf, s, _ = jacobi_svd(F)
+    U = Uf[:, :k]
+    idx = np.argmax(np.abs(U), axis=0)
+    U = U * np.where(U[idx, np.arange(k)] < 0, -1.0, 1.0)[None, :]
+    return U, np.maximum(s[:k] ** 2 - nu, 0.0)
 
 
 # ---------------------------------------------------------------------------
