@@ -129,6 +129,8 @@ def make_workload(name, device, rank):
         rp_, ci, va = synth.powerlaw_csr(w["m"], w["n"], w["nnz"], w["exponent"], w["rank"], w["seed"])
         A = tuple(torch.from_numpy(x).to(device) for x in (rp_, ci, va))
         return w, A, None
+    if w.get("kind") == "e2":
+        return w, synth.e2_matrix_torch(w["n"], w["seed"] + rank, device=device), None
     r = min(w["m"], w["n"])
     sigma = w["spectrum"](r)
     A, colsum = synth.haar_dense_torch(w["m"], w["n"], sigma, w["seed"], device=device, return_colsum=True)
@@ -144,6 +146,15 @@ def sigma_k1_csr(A, shape, k):
     S = torch.sparse_csr_tensor(rp_.long(), ci.long(), va, size=shape).to_sparse_coo()
     g = torch.manual_seed(5)
     _, s, _ = torch.svd_lowrank(S, q=k + 30, niter=30)
+    return float(s[k].item())
+
+
+def sigma_k1_lowrank(A, k):
+    """sigma_{k+1} of a large dense A by an independent randomized SVD (torch.svd_lowrank,
+    q = k + 30, 12 power iterations) -- measurement only."""
+    import torch
+    torch.manual_seed(5)
+    _, s, _ = torch.svd_lowrank(A, q=k + 30, niter=12)
     return float(s[k].item())
 
 
@@ -320,6 +331,8 @@ def run_reference(args):
     w = dict(synth.WORKLOADS[args.workload])
     if w.get("kind") == "batched":
         return run_reference_batched(args, w)
+    if w.get("kind") == "e2":
+        return run_reference_square(args, w)
     r = min(w["m"], w["n"])
     # size each step's row sample so that warmup + steps take about ref_budget seconds
     probe_rows = max(w["l"] + 1, min(w["m"], 4000))
@@ -346,6 +359,38 @@ def run_reference(args):
                    "its": w["its"], "raw": w["raw"], "format": w.get("kind", "dense")},
         "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
                          "sample": f"FP64 numpy/scipy oracle on the first {rows} of {w['m']} rows, time scaled by m"},
+        "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_square(args, w):
+    """The oracle on a smaller n_s x n_s matrix of the same law (Section 7's importance-of-
+    power-iterations matrix), n_s sized to the time budget, its time scaled by m n / n_s^2."""
+    import oracle
+    import synth
+
+    def once(ns):
+        a = synth.e2_matrix_np(ns, w["seed"])
+        t0 = time.perf_counter()
+        oracle.rpca(a, w["k"], w["l"], w["its"], raw=w["raw"], seed=1)
+        return time.perf_counter() - t0
+    t_probe = once(1000)
+    per_step = args.ref_budget / max(args.steps + args.warmup, 1)
+    ns = int(min(w["n"], max(1000, 1000 * (per_step / max(t_probe, 1e-9)) ** 0.5)))
+    for _ in range(args.warmup):
+        once(ns)
+    ts = [once(ns) for _ in range(args.steps)]
+    per_full = (sum(ts) / len(ts)) * (w["m"] / ns) * (w["n"] / ns)
+    value = 1.0 / per_full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "PCA/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"],
+                   "its": w["its"], "raw": w["raw"], "format": "dense"},
+        "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"FP64 numpy oracle on a {ns} x {ns} matrix of the same law, time scaled by mn"},
         "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -747,6 +792,9 @@ def main():
     if csr:
         sk1 = sigma_k1_csr(A, (m, n), k)
         sk1_how = "torch.svd_lowrank (q = k + 30, 30 power iterations)"
+    elif w.get("kind") == "e2":
+        sk1 = sigma_k1_lowrank(A, k)
+        sk1_how = "torch.svd_lowrank (q = k + 30, 12 power iterations)"
     elif n <= 4096 or raw:
         sk1 = sigma_k1_reference(A, k, raw)
         sk1_how = "FP64 Gram of the centred stored matrix, eigvalsh"
@@ -971,6 +1019,14 @@ def main():
         forms["plain_fp32"] = {"its": its, "value": world / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
                                "steps": side_steps, "resid_over_sigma_k1": est_fp32 / sk1,
                                "speedup_of_headline": ms_fp32 / ms_per_step}
+        if w.get("its_sweep"):
+            # Section 7's study of the number of power iterations on this workload
+            sweep = {}
+            for its_s in w["its_sweep"]:
+                ms_s = time_form(args.precision, its_s)
+                sweep[str(its_s)] = {"value": world / (ms_s / 1e3), "ms_per_step": ms_s,
+                                     "resid_over_sigma_k1": estimate(args.resid_iters_conv) / sk1}
+            forms["its_sweep"] = sweep
         if l <= 160 and its > 0:
             # Section 5's LU renormalisation (tall-skinny LU) in place of CholeskyQR
             ms_lu = time_form(args.precision, its, renorm="lu")
@@ -981,17 +1037,30 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if csr:
+        if w.get("kind") == "e2":
+            import oracle
+            ns = 4000
+            A_small = synth.e2_matrix_np(ns, w["seed"])
+            t0 = time.perf_counter()
+            oracle.rpca(A_small, k, l, its, raw=raw, seed=1)
+            t = (time.perf_counter() - t0) * (m / ns) * (n / ns)
+            rows = None
+        elif csr:
             import scipy.sparse as sp
             A_host = sp.csr_matrix((A[2].cpu().numpy(), A[1].cpu().numpy(), A[0].cpu().numpy()), shape=(m, n))
             rows = min(m, 200000)
         else:
             A_host = A[: min(m, args.ref_rows)].cpu().numpy()
             rows = A_host.shape[0]
-        t = oracle_sample(A_host, w, rows)
-        cpu = {"value": 1.0 / (t * m / rows), "unit": "PCA/s", "cores": cores(), "kind": "oracle",
-               "sample": f"one FP64 numpy oracle PCA on the first {rows} of {m} rows "
-                         f"({t:.1f} s), time scaled by m"}
+        if rows is None:
+            cpu = {"value": 1.0 / t, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
+                   "sample": f"one FP64 numpy oracle PCA of a {ns} x {ns} matrix of the same law "
+                             f"({t * (ns / m) * (ns / n):.1f} s), time scaled by m n"}
+        else:
+            t = oracle_sample(A_host, w, rows)
+            cpu = {"value": 1.0 / (t * m / rows), "unit": "PCA/s", "cores": cores(), "kind": "oracle",
+                   "sample": f"one FP64 numpy oracle PCA on the first {rows} of {m} rows "
+                             f"({t:.1f} s), time scaled by m"}
 
     if rank != 0:
         if world > 1:

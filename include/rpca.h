@@ -70,8 +70,17 @@ typedef enum rpca_precision {
 
 typedef enum rpca_renorm {
     RPCA_RENORM_CHOLQR = 0,      /* Gram + Cholesky renormalisation (span-equivalent to LU) */
-    RPCA_RENORM_LU = 1           /* tall-skinny LU with tournament pivoting (Section 5's lu);
+    RPCA_RENORM_LU = 1,          /* tall-skinny LU with tournament pivoting (Section 5's lu);
                                     dense and CSR with l <= 160, else RPCA_ERR_UNSUPPORTED */
+    /* Flag, or'ed into either kind: renormalise only after the odd-numbered products
+     * (Section 5, last paragraph).  Products are numbered in the order they are
+     * applied -- the sketch is the first, then A^* and A alternate (rpca_dense,
+     * rpca_csr); one product with A per iteration (rpca_sym, rpca_nystrom) -- so the
+     * general method applies A (A^* Q) unrenormalised.  The final orthonormalisation
+     * always runs.  Fewer renormalisations, less accuracy: when sigma_1 / sigma_l of
+     * the sketch exceeds about u^-1/2 (u = 2^-24), the trailing directions are lost.
+     * Not for rpca_batched (RPCA_ERR_UNSUPPORTED). */
+    RPCA_RENORM_ODD_ONLY = 4
 } rpca_renorm;
 
 typedef struct rpca_opts {
@@ -81,7 +90,8 @@ typedef struct rpca_opts {
     int32_t raw;                 /* nonzero: approximate A itself, no column centring */
     uint64_t seed;               /* Philox key for Omega (stream 0) */
     int32_t precision;           /* rpca_precision */
-    int32_t renorm;              /* rpca_renorm, for every renormalisation but the last */
+    int32_t renorm;              /* rpca_renorm kind (| RPCA_RENORM_ODD_ONLY), for every
+                                    renormalisation but the last */
     const float *omega;          /* optional caller-supplied Omega (n x l, row-major,
                                     leading dimension l, device); NULL = Philox */
     const float *col_weights;    /* optional d (n, device): the sketch uses diag(d) Omega;
@@ -125,6 +135,40 @@ size_t rpca_csr_workspace_size(int64_t m, int64_t n, int64_t nnz, const rpca_opt
 int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
              const float *val, const rpca_opts *o, float *U, int64_t ldu, float *S,
              float *V, int64_t ldv, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Self-adjoint A (n x n, symmetric): Section 5's loop, which applies only A
+ * (A^* = A).  Q starts as Omega (n x l, as in rpca_dense); for it = 1..its:
+ * Q = A Q, renormalised (o->renorm; LU or CholeskyQR) when it < its and
+ * orthonormalised when it == its.  Then B = Q^T A Q (l x l, symmetrised), its
+ * SVD B = W diag(S) Z^T, U = Q W, V = Q Z (Eqs. i2-i4 with the projection taken
+ * on both sides, so that the approximation is self-adjoint): A ~ U diag(S) V^T
+ * with V = U diag(sign(lambda)), i.e. A ~ U diag(lambda) U^T where lambda_j =
+ * +-S_j are the k eigenvalues of largest magnitude.  Signs: V's columns as in
+ * rpca_dense, U's columns flipped with them.
+ * o->raw must be nonzero (A is used as it is: centring would break the
+ * symmetry) and o->its >= 1, else RPCA_ERR_INVALID_ARG.  Only the upper and
+ * lower triangles' agreement is assumed, not checked.  A: lda >= n, device.
+ * U, V: n x k (ldu, ldv >= k); S: k, descending.  ws as rpca_dense.
+ * ---------------------------------------------------------------------- */
+size_t rpca_sym_workspace_size(int64_t n, const rpca_opts *o);
+int rpca_sym(const float *A, int64_t n, int64_t lda, const rpca_opts *o, float *U, int64_t ldu,
+             float *S, float *V, int64_t ldv, void *ws, size_t ws_bytes, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Stabilised Nystrom approximation of a self-adjoint, nonnegative-definite A
+ * (Section 3): A ~ U diag(S) U^T.
+ * Q: rpca_sym's range finder.  Then, for A + nu I with
+ * nu = 2 (16 l + sqrt(n)) 2^-24 tr(Q^T A Q) (Section 3 adds a multiple of the
+ * identity and subtracts it again; this size keeps the l x l Cholesky of the
+ * FP32 arithmetic clear of breakdown):
+ *   B1 = A Q + nu Q;  B2 = Q^T B1 (symmetrised);  C^T C = B2 (Cholesky);
+ *   F = B1 C^-1;  F = U Sigma W^T (SVD);  S = max(Sigma^2 - nu, 0).
+ * U: n x k (ldu >= k), each column's largest-magnitude entry positive; S: k,
+ * descending.  Other arguments and requirements as rpca_sym (no V).
+ * ---------------------------------------------------------------------- */
+int rpca_nystrom(const float *A, int64_t n, int64_t lda, const rpca_opts *o, float *U, int64_t ldu,
+                 float *S, void *ws, size_t ws_bytes, rpca_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched randomized PCA of many small dense matrices in one launch (the same

@@ -494,11 +494,15 @@ def nystrom_shift(B2: np.ndarray, n: int) -> float:
     """The multiple nu of the identity added to A (and subtracted from the result).
 
     Section 3 leaves its size open ("an appropriate multiple"); the reading
-    taken is nu = sqrt(n) u tr(B2) with u = 2^-24: the FP32 rounding of the
-    n-term products that form B2 = Q^* A Q is about sqrt(n) u |A| per entry,
-    and tr(B2) bounds |B2|, so B2 + nu I stays positive definite.
+    taken is nu = 2 (16 l + sqrt(n)) u tr(B2) with u = 2^-24 and B2 = Q^* A Q
+    (l x l): twice the sum of the pivot size below which an FP32 Cholesky of
+    an l x l matrix is taken to have collapsed (16 l u of a diagonal entry)
+    and the FP32 rounding of the n-term products that form B2 (about
+    sqrt(n) u |A| per entry), relative to tr(B2) >= |B2|.  Then B2 + nu I is
+    safely positive definite in FP32 arithmetic.
     """
-    return math.sqrt(n) * NYSTROM_U * float(np.trace(B2))
+    l = B2.shape[0]
+    return 2.0 * (16.0 * l + math.sqrt(n)) * NYSTROM_U * float(np.trace(B2))
 
 
 def nystrom(A, k: int, l: int | None = None, its: int = 2, seed: int = 0,

@@ -25,6 +25,7 @@ RPCA_MLP_PACKED_BYTES = 38416
 
 PREC = {"fp32": 0, "bf16x3": 1}
 RENORM = {"cholqr": 0, "lu": 1}
+RPCA_RENORM_ODD_ONLY = 4
 
 
 class RpcaOpts(C.Structure):
@@ -42,6 +43,9 @@ SIGNATURES = [
     ("rpca_default_opts", None, [_OPTS, _I32]),
     ("rpca_dense_workspace_size", _SZ, [_I64, _I64, _OPTS]),
     ("rpca_dense", C.c_int, [_P, _I64, _I64, _I64, _OPTS, _P, _I64, _P, _P, _I64, _P, _SZ, _P]),
+    ("rpca_sym_workspace_size", _SZ, [_I64, _OPTS]),
+    ("rpca_sym", C.c_int, [_P, _I64, _I64, _OPTS, _P, _I64, _P, _P, _I64, _P, _SZ, _P]),
+    ("rpca_nystrom", C.c_int, [_P, _I64, _I64, _OPTS, _P, _I64, _P, _P, _SZ, _P]),
     ("rpca_csr_workspace_size", _SZ, [_I64, _I64, _I64, _OPTS]),
     ("rpca_csr", C.c_int, [_I64, _I64, _I64, _P, _P, _P, _OPTS, _P, _I64, _P, _P, _I64, _P, _SZ, _P]),
     ("rpca_resid_workspace_size", _SZ, [_I64, _I64, _I32]),

@@ -630,7 +630,7 @@ extern "C" int rpca_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *row_pt
     if (!o || !rpca::csr_args_ok(m, n, nnz, row_ptr, col_idx, val)) return RPCA_ERR_INVALID_ARG;
     const size_t need = rpca_csr_workspace_size(m, n, nnz, o);
     RPCA_TRY(rpca::check_common(m, n, o, U, ldu, S, V, ldv, ws, ws_bytes, need));
-    if (o->renorm == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
+    if (rpca::renorm_kind(o->renorm) == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     const int lp = rpca::padded_l(o->l);
     const rpca::CsrScratch SC = rpca::csr_scratch(m, n, nnz, lp);

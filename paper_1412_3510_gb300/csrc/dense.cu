@@ -63,13 +63,53 @@ extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, con
     if (!A || !o || lda < n) return RPCA_ERR_INVALID_ARG;
     const size_t need = rpca_dense_workspace_size(m, n, o);
     RPCA_TRY(rpca::check_common(m, n, o, U, ldu, S, V, ldv, ws, ws_bytes, need));
-    if (o->renorm == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
+    if (rpca::renorm_kind(o->renorm) == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
     rpca::DenseOp op;
     op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
     const int lp = rpca::padded_l(o->l);
     const int splits = std::max(rpca::choose_splits(n, lp, m), rpca::tc_adjoint_splits(n, m, lp));
     const rpca::Layout L = rpca::make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp));
     return rpca::run_pipeline(op, o, U, ldu, S, V, ldv, ws, L, (cudaStream_t)stream);
+}
+
+namespace {
+
+// The arguments of rpca_sym and rpca_nystrom: a square A used as it is.
+int check_sym(const float *A, int64_t n, int64_t lda, const rpca_opts *o, const float *U, int64_t ldu,
+              const float *S, const void *ws, size_t ws_bytes) {
+    if (!A || !o || !U || !S || n < 1 || lda < n) return RPCA_ERR_INVALID_ARG;
+    if (!o->raw || o->its < 1) return RPCA_ERR_INVALID_ARG;
+    const size_t need = rpca_sym_workspace_size(n, o);
+    // check_common validates k, l, its, precision and renorm; V is checked by the caller
+    return rpca::check_common(n, n, o, U, ldu, S, U, ldu, ws, ws_bytes, need);
+}
+
+int run_sym(const float *A, int64_t n, int64_t lda, const rpca_opts *o, bool nystrom, float *U, int64_t ldu,
+            float *S, float *V, int64_t ldv, void *ws, rpca_stream_t stream) {
+    if (rpca::renorm_kind(o->renorm) == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
+    rpca::DenseOp op;
+    op.m = n; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
+    const int lp = rpca::padded_l(o->l);
+    const int splits = std::max(rpca::choose_splits(n, lp, n), rpca::tc_adjoint_splits(n, n, lp));
+    const rpca::Layout L = rpca::make_layout(n, n, o->l, o->k, splits, op.scratch_bytes(lp));
+    return rpca::run_pipeline_sym(op, o, nystrom, U, ldu, S, V, ldv, ws, L, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" size_t rpca_sym_workspace_size(int64_t n, const rpca_opts *o) { return rpca_dense_workspace_size(n, n, o); }
+
+extern "C" int rpca_sym(const float *A, int64_t n, int64_t lda, const rpca_opts *o, float *U, int64_t ldu,
+                        float *S, float *V, int64_t ldv, void *ws, size_t ws_bytes, rpca_stream_t stream) {
+    RPCA_TRY(check_sym(A, n, lda, o, U, ldu, S, ws, ws_bytes));
+    if (!V || ldv < o->k) return RPCA_ERR_INVALID_ARG;
+    return run_sym(A, n, lda, o, false, U, ldu, S, V, ldv, ws, stream);
+}
+
+extern "C" int rpca_nystrom(const float *A, int64_t n, int64_t lda, const rpca_opts *o, float *U, int64_t ldu,
+                            float *S, void *ws, size_t ws_bytes, rpca_stream_t stream) {
+    RPCA_TRY(check_sym(A, n, lda, o, U, ldu, S, ws, ws_bytes));
+    return run_sym(A, n, lda, o, true, U, ldu, S, nullptr, 0, ws, stream);
 }
 
 namespace rpca {

@@ -18,6 +18,8 @@
 // the padded width lp = round_up(l + 1, 8); column l of a Q that enters an
 // adjoint product holds ones (it carries m c through A^T), every other padding
 // column holds zeros.
+#include <cmath>
+
 #include "pipeline.cuh"
 #include "tc_gemm.cuh"
 #include "timing.cuh"
@@ -40,6 +42,52 @@ __global__ void copy_scale_kernel(int64_t n, int l, const float *__restrict__ sr
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Symmetric part of the reduced l x l matrix G (row stride ldg): out[i][j] =
+// (G[i][j] + G[j][i]) / 2 for i, j < l, row stride ldo, zero padding up to ldo.  With
+// nu_out, also nu = nu_scale * trace(G) added to the diagonal and stored to *nu_out
+// (the identity shift of the Nystrom method).  One CTA.
+__global__ void __launch_bounds__(256)
+symmetrize_kernel(const float *__restrict__ G, int l, int ldg, float *__restrict__ out, int ldo, float nu_scale,
+                  float *__restrict__ nu_out) {
+    __shared__ float red[256];
+    float nu = 0.f;
+    if (nu_out) {
+        float t = 0.f;
+        for (int i = threadIdx.x; i < l; i += blockDim.x) t += G[(size_t)i * ldg + i];
+        red[threadIdx.x] = t;
+        __syncthreads();
+        for (int off = 128; off > 0; off >>= 1) {
+            if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+            __syncthreads();
+        }
+        nu = nu_scale * red[0];
+        if (threadIdx.x == 0) *nu_out = nu;
+    }
+    for (int e = threadIdx.x; e < ldo * ldo; e += blockDim.x) {
+        const int i = e / ldo, j = e - i * ldo;
+        float v = 0.f;
+        if (i < l && j < l) v = 0.5f * (G[(size_t)i * ldg + j] + G[(size_t)j * ldg + i]) + (i == j ? nu : 0.f);
+        out[e] = v;
+    }
+}
+
+// Y[i][c] += nu Q[i][c] for c < l (nu read from the device).
+__global__ void __launch_bounds__(256)
+add_scaled_kernel(float *__restrict__ Y, const float *__restrict__ Q, int64_t rows, int l, int lp,
+                  const float *__restrict__ nu_p) {
+    const float nu = *nu_p;
+    const int64_t total = rows * (int64_t)lp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        if ((int)(e % lp) < l) Y[e] = fmaf(nu, Q[e], Y[e]);
+}
+
+// S[r] = max(sig[r]^2 - nu, 0): Section 3's Sigma = S^2 with the shift taken back.
+__global__ void nystrom_values_kernel(float *__restrict__ S, const float *__restrict__ sig, int k,
+                                      const float *__restrict__ nu_p) {
+    const float nu = *nu_p;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) S[r] = fmaxf(fmaf(sig[r], sig[r], -nu), 0.f);
+}
 
 }  // namespace
 
@@ -77,6 +125,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.zbuf = take(256);
     L.rinv_m = take(lp * lp * 4);
     L.flags = take(256);
+    L.scal = take(256);
     L.lu0 = take(tslu_ids_bytes(std::max(m, n), l));
     L.lu1 = take(tslu_ids_bytes(std::max(m, n), l));
     L.rsplit = take(tc_rmul_split_bytes(L.lp));
@@ -94,7 +143,8 @@ int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64
     if (o->its < 0 || o->its > 1000) return RPCA_ERR_INVALID_ARG;
     if (ldu < o->k || ldv < o->k) return RPCA_ERR_INVALID_ARG;
     if (o->precision != RPCA_PREC_FP32 && o->precision != RPCA_PREC_BF16X3) return RPCA_ERR_INVALID_ARG;
-    if (o->renorm != RPCA_RENORM_CHOLQR && o->renorm != RPCA_RENORM_LU) return RPCA_ERR_INVALID_ARG;
+    if (renorm_kind(o->renorm) != RPCA_RENORM_CHOLQR && renorm_kind(o->renorm) != RPCA_RENORM_LU)
+        return RPCA_ERR_INVALID_ARG;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
     return RPCA_OK;
 }
@@ -232,12 +282,13 @@ int adjoint_pass(const Operator &op, const Ctx &c, bool raw, const float *q, boo
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status) {
     Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status),
-          o->renorm == RPCA_RENORM_LU};
+          renorm_kind(o->renorm) == RPCA_RENORM_LU};
     op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
     op.st = c.st;
     const bool raw = o->raw != 0;
+    const bool odd_only = renorm_odd_only(o->renorm);
     const int l = L.l, lp = L.lp;
-    float *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
+    float *x0 = c.at<float>(L.x0), *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
 
     if (clear_status && cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
     if (cudaMemsetAsync(x1, 0, (size_t)L.n * lp * 4, s) != cudaSuccess) return RPCA_ERR_CUDA;
@@ -251,19 +302,20 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
         RPCA_TRY(launch_omega(L.n, l, o->seed, 0, o->col_weights, x1, lp, s));
     }
 
-    auto apply = [&]() {
+    auto apply = [&](const float *X) {
         TimedScope ts(kTimeApply, s);
-        return op.apply(x1, lp, y0, s);
+        return op.apply(X, lp, y0, s);
     };
-    // sketch and power iterations
+    // sketch and power iterations; odd-only: the products with A^* (the even-numbered
+    // ones) feed the next product with A unrenormalised (x0's padding columns are zero)
     const float *q = nullptr;
     bool pending = false;
-    RPCA_TRY(apply());
+    RPCA_TRY(apply(x1));
     RPCA_TRY(renorm_m(c, raw, o->its == 0, &q, &pending));
     for (int it = 1; it <= o->its; ++it) {
         RPCA_TRY(adjoint_pass(op, c, raw, q, pending));
-        RPCA_TRY(renorm_n(c, false));
-        RPCA_TRY(apply());
+        if (!odd_only) RPCA_TRY(renorm_n(c, false));
+        RPCA_TRY(apply(odd_only ? x0 : x1));
         RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending));
     }
 
@@ -284,6 +336,125 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     if (tc_rmul_ok(L.m, L.k) && (reinterpret_cast<uintptr_t>(U) & 3u) == 0)
         return launch_tc_rmul(y1, L.m, lp, wk, L.kp, L.k, c.at<__nv_bfloat16>(L.rsplit), U, ldu, nullptr, c.st, s);
     RPCA_TRY(launch_sgemm(false, L.m, L.k, lp, y1, lp, wk, L.kp, U, ldu, 1, 0, s));
+    return RPCA_OK;
+}
+
+// Self-adjoint A (n x n, m == n in the layout).  Section 5's loop: Q = A Q each
+// iteration, renormalised (LU or CholeskyQR) when it < its -- only in the odd
+// iterations with RPCA_RENORM_ODD_ONLY -- and orthonormalised (CholeskyQR two or three
+// times) when it == its.  Blocks ping-pong between y0 and x0 (both n x lp here);
+// renormalised blocks go to x1, the final Q to y1.
+int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, int64_t ldu, float *S, float *V,
+                     int64_t ldv, void *ws, const Layout &L, cudaStream_t s) {
+    Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status),
+          renorm_kind(o->renorm) == RPCA_RENORM_LU};
+    op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
+    op.st = c.st;
+    const bool odd_only = renorm_odd_only(o->renorm);
+    const int l = L.l, lp = L.lp;
+    const int64_t n = L.n;
+    float *x0 = c.at<float>(L.x0), *x1 = c.at<float>(L.x1), *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
+    float *nu = c.at<float>(L.scal);
+    if (cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (cudaMemsetAsync(x1, 0, (size_t)n * lp * 4, s) != cudaSuccess) return RPCA_ERR_CUDA;
+    if (o->omega) {
+        const int64_t grid = std::min<int64_t>(cdiv(n * (int64_t)l, 256), (int64_t)num_sms() * 8);
+        copy_scale_kernel<<<(unsigned)grid, 256, 0, s>>>(n, l, o->omega, l, o->col_weights, x1, lp);
+        RPCA_CHECK_LAUNCH();
+    } else {
+        RPCA_TRY(launch_omega(n, l, o->seed, 0, o->col_weights, x1, lp, s));
+    }
+    auto apply = [&](const float *X, float *Y) {
+        TimedScope ts(kTimeApply, s);
+        return op.apply(X, lp, Y, s);
+    };
+    const float *cur = x1;
+    for (int it = 1; it <= o->its; ++it) {
+        float *out = cur == y0 ? x0 : y0;
+        RPCA_TRY(apply(cur, out));
+        if (it == o->its) {
+            int *flag = c.at<int>(L.flags);
+            float *other = out == y0 ? x0 : y0;
+            RPCA_TRY(cholqr_round(c, out, y1, n, L.s_gram_m, nullptr, nullptr, flag));
+            RPCA_TRY(cholqr_round(c, y1, other, n, L.s_gram_m, nullptr, nullptr));
+            RPCA_TRY(cholqr_round(c, other, y1, n, L.s_gram_m, nullptr, nullptr, nullptr, flag));
+        } else if (!odd_only || it % 2 == 1) {
+            if (c.lu) {
+                float *rinv = c.at<float>(L.rinv);
+                RPCA_TRY(lu_factor(c, out, n, rinv));
+                TimedScope ts(kTimeTrsm, s);
+                RPCA_TRY(launch_sgemm(false, n, lp, lp, out, lp, rinv, lp, x1, lp, 1, 0, s));
+            } else {
+                RPCA_TRY(cholqr_round(c, out, x1, n, L.s_gram_m, nullptr, nullptr));
+            }
+            cur = x1;
+        } else {
+            cur = out;
+        }
+    }
+    RPCA_TRY(launch_finalize(y1, n, l, lp, 0.f, nullptr, s));
+
+    // B = Q^T (A Q): split-K partials and their compensated reduction
+    RPCA_TRY(apply(y1, y0));
+    float *part = c.at<float>(L.part), *G = c.at<float>(L.G);
+    {
+        TimedScope ts(kTimeGram, s);
+        RPCA_TRY(launch_sgemm(true, lp, lp, n, y1, lp, y0, lp, part, lp, L.s_gram_m, (int64_t)lp * lp, s));
+        RPCA_TRY(launch_gram_reduce(part, L.s_gram_m, l, lp, G, s));
+    }
+    float *wk = c.at<float>(L.wk), *zk = c.at<float>(L.zk), *sig = c.at<float>(L.sig);
+    float *racc0 = c.at<float>(L.racc0);
+    if (!nystrom) {
+        // symmetric B = W Sigma Z^T (Jacobi); U = Q W, V = Q Z (Eqs. i3, i4 with B = Q^T A Q)
+        symmetrize_kernel<<<1, 256, 0, s>>>(G, l, gram_ld(l), racc0, l, 0.f, nullptr);
+        RPCA_CHECK_LAUNCH();
+        {
+            TimedScope ts(kTimeSmallSvd, s);
+            RPCA_TRY(launch_small_svd(racc0, l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot), c.at<float>(L.zbuf),
+                                      c.at<int>(L.perm), c.st, s));
+        }
+        TimedScope ts_lift(kTimeLift, s);
+        RPCA_TRY(launch_sgemm(false, n, L.k, lp, y1, lp, zk, L.kp, V, ldv, 1, 0, s));
+        RPCA_TRY(launch_sign_fix(V, n, ldv, L.k, wk, lp, L.kp, sig, S, s));
+        return launch_sgemm(false, n, L.k, lp, y1, lp, wk, L.kp, U, ldu, 1, 0, s);
+    }
+    // Section 3 with A + nu I: B1 = A Q + nu Q, B2 = Q^T B1 = sym(Q^T A Q) + nu I,
+    // C^T C = B2, F = B1 C^-1, F = Q2 R (CholeskyQR), R^T = W Sigma Z^T, so the left
+    // singular vectors of F are Q2 Z and its singular values Sigma; S = Sigma^2 - nu.
+    // nu = 2 (16 l + sqrt(n)) 2^-24 tr(B2): twice the FP32 Cholesky's collapse threshold
+    // (16 l u of a diagonal entry) plus the rounding of the n-term products behind B2.
+    float *B2 = c.at<float>(L.rinv_m);
+    const float nu_scale = (float)(2.0 * (16.0 * l + std::sqrt((double)n)) * 0x1p-24);
+    symmetrize_kernel<<<1, 256, 0, s>>>(G, l, gram_ld(l), B2, gram_ld(l), nu_scale, nu);
+    RPCA_CHECK_LAUNCH();
+    {
+        const int64_t grid = std::min<int64_t>(cdiv(n * (int64_t)lp, 256), (int64_t)num_sms() * 8);
+        add_scaled_kernel<<<(unsigned)grid, 256, 0, s>>>(y0, y1, n, l, lp, nu);
+        RPCA_CHECK_LAUNCH();
+    }
+    float *rinv = c.at<float>(L.rinv);
+    {
+        TimedScope ts(kTimeChol, s);
+        RPCA_TRY(launch_chol_inv(B2, l, lp, rinv, nullptr, nullptr, c.st, s));
+    }
+    {
+        TimedScope ts(kTimeTrsm, s);
+        if (tc_rmul_ok(n, lp))
+            RPCA_TRY(launch_tc_rmul(y0, n, lp, rinv, lp, lp, c.at<__nv_bfloat16>(L.rsplit), x0, lp, nullptr, c.st, s));
+        else
+            RPCA_TRY(launch_sgemm(false, n, lp, lp, y0, lp, rinv, lp, x0, lp, 1, 0, s));
+    }
+    RPCA_TRY(renorm_n(c, true));
+    {
+        TimedScope ts(kTimeSmallSvd, s);
+        RPCA_TRY(launch_small_svd(racc0, l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot), c.at<float>(L.zbuf),
+                                  c.at<int>(L.perm), c.st, s));
+    }
+    TimedScope ts_lift(kTimeLift, s);
+    RPCA_TRY(launch_sgemm(false, n, L.k, lp, x1, lp, zk, L.kp, U, ldu, 1, 0, s));
+    RPCA_TRY(launch_sign_fix(U, n, ldu, L.k, wk, lp, L.kp, sig, S, s));
+    nystrom_values_kernel<<<1, 256, 0, s>>>(S, sig, L.k, nu);
+    RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
 

@@ -26,7 +26,7 @@ struct Layout {
     int s_adj = 0, s_gram_m = 0, s_gram_n = 0, cchunks = 0;
     size_t status = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, part = 0, cpart = 0, qpart = 0, G = 0,
            rinv = 0, racc0 = 0, racc1 = 0, wk = 0, zk = 0, sig = 0, perm = 0, rot = 0, zbuf = 0,
-           rinv_m = 0, flags = 0, lu0 = 0, lu1 = 0, rsplit = 0, scratch = 0, total = 0;
+           rinv_m = 0, flags = 0, scal = 0, lu0 = 0, lu1 = 0, rsplit = 0, scratch = 0, total = 0;
 };
 
 Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_t op_scratch);
@@ -39,6 +39,17 @@ int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64
 // Run the whole method (Sections 2 and 5; Eqs. i1-i4) on operator `op`.
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status = true);
+
+// Self-adjoint A (m == n): Section 5's loop (products with A only), then either the
+// two-sided projection B = Q^T A Q and its SVD (nystrom == false: A ~ U diag(S) V^T with
+// V = U diag(sign(lambda))), or Section 3's stabilised Nystrom method (nystrom == true:
+// A ~ U diag(S) U^T, V unused).
+int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, int64_t ldu, float *S, float *V,
+                     int64_t ldv, void *ws, const Layout &L, cudaStream_t s);
+
+// Renormalisation kind and the odd-only flag of rpca_opts::renorm.
+inline int renorm_kind(int renorm) { return renorm & ~RPCA_RENORM_ODD_ONLY; }
+inline bool renorm_odd_only(int renorm) { return (renorm & RPCA_RENORM_ODD_ONLY) != 0; }
 
 // Offset of the small SVD's singular values in rpca_dense's workspace.
 size_t dense_sigma_offset(int64_t m, int64_t n, const float *A, int64_t lda, const rpca_opts *o);

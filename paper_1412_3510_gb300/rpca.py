@@ -51,7 +51,7 @@ def _rowmajor_ld(t: torch.Tensor, name: str) -> int:
 
 
 def make_opts(k, l=None, its=2, raw=False, seed=0, precision="fp32", renorm="cholqr",
-              omega=None, col_weights=None) -> L.RpcaOpts:
+              omega=None, col_weights=None, odd_only=False) -> L.RpcaOpts:
     o = L.RpcaOpts()
     o.k = int(k)
     o.l = int(k + 2 if l is None else l)
@@ -59,7 +59,7 @@ def make_opts(k, l=None, its=2, raw=False, seed=0, precision="fp32", renorm="cho
     o.raw = int(bool(raw))
     o.seed = int(seed) & ((1 << 64) - 1)
     o.precision = L.PREC[precision]
-    o.renorm = L.RENORM[renorm]
+    o.renorm = L.RENORM[renorm] | (L.RPCA_RENORM_ODD_ONLY if odd_only else 0)
     o.omega = None if omega is None else omega.data_ptr()
     o.col_weights = None if col_weights is None else col_weights.data_ptr()
     return o
@@ -77,7 +77,8 @@ def workspace(nbytes: int, device) -> torch.Tensor:
 def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw: bool = False,
                seed: int = 0, precision: str = "fp32", renorm: str = "cholqr",
                omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
-               ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+               ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
+               odd_only: bool = False):
     """Randomized PCA A_c ~ U diag(S) V^T (Sections 2 and 5 of the paper).
 
     A: m x n float32 CUDA tensor, row-major (any leading dimension >= n).
@@ -93,7 +94,7 @@ def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw:
     if col_weights is not None:
         _need_cuda(col_weights, "col_weights")
         col_weights = col_weights.contiguous()
-    opts = make_opts(k, l, its, raw, seed, precision, renorm, omega, col_weights)
+    opts = make_opts(k, l, its, raw, seed, precision, renorm, omega, col_weights, odd_only)
     lib = L.load()
     need = rpca_dense_workspace_size(m, n, opts)
     if need == 0:
@@ -116,6 +117,58 @@ def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw:
         status = rpca_read_status(ws, stream)
         _check(status, "rpca_dense (device)")
     return U, S, V
+
+
+def _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, nystrom):
+    _need_cuda(A, "A")
+    lda = _rowmajor_ld(A, "A")
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("A must be square")
+    if omega is not None:
+        _need_cuda(omega, "omega")
+        omega = omega.contiguous()
+    opts = make_opts(k, l, its, True, seed, precision, renorm, omega, None, odd_only)
+    lib = L.load()
+    need = int(lib.rpca_sym_workspace_size(n, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_sym_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if out is None:
+        U = torch.empty(n, k, dtype=torch.float32, device=A.device)
+        S = torch.empty(k, dtype=torch.float32, device=A.device)
+        V = None if nystrom else torch.empty(n, k, dtype=torch.float32, device=A.device)
+    else:
+        U, S, V = (tuple(out) + (None,))[:3]
+    if nystrom:
+        code = lib.rpca_nystrom(_ptr(A), n, lda, C.byref(opts), _ptr(U), _rowmajor_ld(U, "U"), _ptr(S), _ptr(ws),
+                                ws.numel(), _stream(stream))
+    else:
+        code = lib.rpca_sym(_ptr(A), n, lda, C.byref(opts), _ptr(U), _rowmajor_ld(U, "U"), _ptr(S), _ptr(V),
+                            _rowmajor_ld(V, "V"), _ptr(ws), ws.numel(), _stream(stream))
+    name = "rpca_nystrom" if nystrom else "rpca_sym"
+    _check(code, name)
+    if check:
+        _check(rpca_read_status(ws, stream), name + " (device)")
+    return (U, S) if nystrom else (U, S, V)
+
+
+def rpca_sym(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, seed: int = 0,
+             precision: str = "fp32", renorm: str = "cholqr", omega: torch.Tensor | None = None,
+             odd_only: bool = False, ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+    """Self-adjoint A (n x n): Section 5's loop of products with A only, then
+    B = Q^T A Q; returns (U, S, V) with A ~ U diag(S) V^T, V = U diag(sign(lambda))."""
+    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, False)
+
+
+def rpca_nystrom(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, seed: int = 0,
+                 precision: str = "fp32", renorm: str = "cholqr", omega: torch.Tensor | None = None,
+                 odd_only: bool = False, ws: torch.Tensor | None = None, out=None, stream=None,
+                 check: bool = True):
+    """Stabilised Nystrom approximation of a nonnegative-definite A (Section 3):
+    returns (U, S) with A ~ U diag(S) U^T."""
+    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, True)
 
 
 def rpca_read_status(ws: torch.Tensor, stream=None) -> int:
@@ -234,7 +287,7 @@ def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, sh
              l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
              omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
              ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
-             renorm: str = "cholqr"):
+             renorm: str = "cholqr", odd_only: bool = False):
     """Randomized PCA of a CSR matrix (row_ptr int32 m+1, col_idx int32 nnz, val float32 nnz)."""
     m, n = int(shape[0]), int(shape[1])
     _need_i32(row_ptr, "row_ptr")
@@ -247,7 +300,7 @@ def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, sh
     if col_weights is not None:
         _need_cuda(col_weights, "col_weights")
         col_weights = col_weights.contiguous()
-    opts = make_opts(k, l, its, raw, seed, "fp32", renorm, omega, col_weights)
+    opts = make_opts(k, l, its, raw, seed, "fp32", renorm, omega, col_weights, odd_only)
     lib = L.load()
     need = int(lib.rpca_csr_workspace_size(m, n, nnz, C.byref(opts)))
     if need == 0:

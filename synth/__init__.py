@@ -29,7 +29,8 @@ import numpy as np
 
 __all__ = [
     "spectrum_exp20", "spectrum_pow15", "spectrum_exp50", "spectrum_section7",
-    "haar_dense_np", "haar_dense_torch", "e2_matrix_np", "propack_diag",
+    "haar_dense_np", "haar_dense_torch", "e2_matrix_np", "e2_matrix_torch", "sym_dense_np", "sym_lowrank_np",
+    "propack_diag",
     "powerlaw_csr", "kernel_matrix_np", "kernel_matrix_torch", "kernel_batch_specs", "KernelSpec",
     "WORKLOADS",
 ]
@@ -157,6 +158,51 @@ def e2_matrix_np(n: int, seed: int) -> np.ndarray:
     odd = ((i[:, None] * i[None, :]) % 2) == 1
     a[odd] = -a[odd]
     return a.astype(np.float32)
+
+
+def e2_matrix_torch(n: int, seed: int, device="cuda", rows_per_chunk: int = 4096):
+    """The same law on a torch device (torch's generator, row chunks), FP32: N(sqrt(30/n), 1)
+    entries, sign flipped where i*j is odd (1-based i, j: both odd)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    a = torch.empty(n, n, dtype=torch.float32, device=device)
+    mu = math.sqrt(30.0 / n)
+    for r0 in range(0, n, rows_per_chunk):
+        r1 = min(n, r0 + rows_per_chunk)
+        blk = torch.randn(r1 - r0, n, generator=g, device=device, dtype=torch.float32)
+        blk += mu
+        # 1-based row r0 + t + 1 is odd when the 0-based row r0 + t is even
+        blk[r0 % 2::2, 0::2] *= -1.0
+        a[r0:r1] = blk
+        del blk
+    return a
+
+
+def sym_dense_np(n: int, lam, seed: int, dtype=np.float32) -> np.ndarray:
+    """Self-adjoint A = Q diag(lam) Q^T with Haar Q (n x n), symmetrised exactly after
+    rounding ((A + A^T) / 2 in the target precision is symmetric bit for bit)."""
+    rng = np.random.default_rng(seed)
+    q = _haar_np(rng, n, n)
+    a = ((q * np.asarray(lam, dtype=np.float64)[None, :]) @ q.T).astype(dtype)
+    return ((a + a.T) / dtype(2)).astype(dtype)
+
+
+def sym_lowrank_np(n: int, lam_top, tail: float, seed: int, psd: bool = False, dtype=np.float32) -> np.ndarray:
+    """Large self-adjoint A without an n x n QR: Q diag(lam_top) Q^T (Q Haar, n x r) plus a
+    tail -- tail * I when psd (nonnegative definite, flat tail), else a symmetric
+    Gaussian matrix scaled to spectral norm about tail (semicircle radius 2 s sqrt(n))."""
+    rng = np.random.default_rng(seed)
+    lam_top = np.asarray(lam_top, dtype=np.float64)
+    q = _haar_np(rng, n, lam_top.size)
+    a = (q * lam_top[None, :]) @ q.T
+    if psd:
+        a[np.arange(n), np.arange(n)] += tail
+    else:
+        g = rng.standard_normal((n, n)) * (tail / (2.0 * math.sqrt(2.0 * n)))
+        a += g + g.T
+    a = a.astype(dtype)
+    return ((a + a.T) / dtype(2)).astype(dtype)
 
 
 def propack_diag(size: int) -> np.ndarray:
@@ -287,6 +333,12 @@ WORKLOADS = {
     # than L2) for profiler captures that must stay small
     "dense_25000x2000_k100": dict(m=25000, n=2000, k=100, l=102, its=2, raw=False,
                                   spectrum=lambda r: spectrum_pow15(r, 1236), seed=1238),
+    # Section 7's importance-of-power-iterations matrix: n x n i.i.d. N(sqrt(30/n), 1), signs
+    # flipped where i*j is odd; rank 4, l = k + 2, its swept over 0, 2, 4; A itself (raw)
+    "e2_gaussian_100000_k4": dict(kind="e2", m=100000, n=100000, k=4, l=6, its=2, raw=True, its_sweep=(0, 2, 4),
+                                  seed=1243),
+    "e2_gaussian_20000_k4": dict(kind="e2", m=20000, n=20000, k=4, l=6, its=2, raw=True, its_sweep=(0, 2, 4),
+                                 seed=1244),
     # sparse: power-law row/column degrees (exponent 2.1), N(0,1) values plus a planted
     # rank-30 part on the pattern
     "csr_1000000x100000_k30": dict(kind="csr", m=1000000, n=100000, nnz=10000000, exponent=2.1, rank=30,
