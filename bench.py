@@ -829,18 +829,23 @@ def main():
     est20 = estimate(args.resid_iters)
     est = estimate(args.resid_iters_conv)
 
-    # one PCA captured as a CUDA graph (the library's launches are stream-ordered and
-    # host-synchronisation free); the stage-timing events are captured with it, so each
-    # replay re-records them and the read-out after the timed region is the last step's
+    # The timed region replays one PCA captured as a CUDA graph (the library's launches
+    # are stream-ordered and free of host synchronisation).  Inside it only the pass
+    # kernels are bracketed by CUDA events: every timed stage adds an event pair to the
+    # graph, and events around all ~50 stages of a PCA would lengthen the step they
+    # measure.  The last replay's events give the pass kernels' durations (roofline); the
+    # stage breakdown comes from a separate, fully instrumented replay afterwards.
+    pass_kinds = (10, 11)
     rp.rpca_timing_reset()
-    rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) + 64)
+    rp.rpca_timing_select(pass_kinds)
+    rp.rpca_timing_enable(True, reserve=4 * (2 * its + 2) + 64)
     graph, per_step_launches = None, None
     if not args.no_graph:
         graph, per_step_launches = capture_graph(rp, step)
     timing_per_step = graph is not None
     if not timing_per_step:
         rp.rpca_timing_reset()
-        rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
+        rp.rpca_timing_enable(True, reserve=4 * (2 * its + 2) * args.steps + 64)
 
     def timed_step():
         if graph is not None:
@@ -874,32 +879,46 @@ def main():
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, world, dev)
     ms_per_step = ms_total / args.steps
     value = job_throughput(world, args.steps, ms_total)
+    covered = 1 if timing_per_step else args.steps          # steps the pass events cover
     try:
-        n_apply, t_apply = rp.rpca_timing_read(0)
-        n_adj, t_adj = rp.rpca_timing_read(1)
-        n_svd, t_svd = rp.rpca_timing_read(3)
-        timed_steps = 1 if timing_per_step else args.steps      # steps the stage events cover
-        extra = {name: rp.rpca_timing_read(kind)[1] / timed_steps
-                 for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
+        n_apply, t_apply = rp.rpca_timing_read(10)
+        n_adj, t_adj = rp.rpca_timing_read(11)
     except Exception as e:                                      # noqa: BLE001
-        # the graph's stage events could not be read: time the stages on eager steps
-        print(f"stage events of the graph unreadable ({e}); stage times from eager steps", file=sys.stderr)
+        # the graph's events could not be read: time the pass kernels on eager steps
+        print(f"pass events of the graph unreadable ({e}); pass times from eager steps", file=sys.stderr)
         rp.rpca_timing_reset()
-        rp.rpca_timing_enable(True, reserve=2 * (12 * its + 30) * args.steps + 64)
+        rp.rpca_timing_enable(True, reserve=4 * (2 * its + 2) * args.steps + 64)
         for _ in range(args.steps):
             step()
         torch.cuda.synchronize()
         rp.rpca_timing_enable(False)
-        timing_per_step = False
-        n_apply, t_apply = rp.rpca_timing_read(0)
-        n_adj, t_adj = rp.rpca_timing_read(1)
-        n_svd, t_svd = rp.rpca_timing_read(3)
-        extra = {name: rp.rpca_timing_read(kind)[1] / args.steps
-                 for name, kind in (("gram", 5), ("chol", 6), ("trsm", 7), ("centre", 8), ("lift", 9))}
+        covered = args.steps
+        n_apply, t_apply = rp.rpca_timing_read(10)
+        n_adj, t_adj = rp.rpca_timing_read(11)
     rp.rpca_timing_reset()
-    if timing_per_step:
-        n_apply, n_adj = n_apply * args.steps, n_adj * args.steps
-        t_apply, t_adj, t_svd = t_apply * args.steps, t_adj * args.steps, t_svd * args.steps
+    n_apply, n_adj = n_apply * args.steps // covered, n_adj * args.steps // covered
+    t_apply, t_adj = t_apply * args.steps / covered, t_adj * args.steps / covered
+
+    # stage breakdown: every stage timed, on separate replays after the timed region
+    rp.rpca_timing_select(None)
+    breakdown_steps = 3
+    rp.rpca_timing_enable(True, reserve=2 * (12 * its + 40) * breakdown_steps + 64)
+    g_stage = capture_graph(rp, step)[0] if graph is not None else None
+    rp.rpca_timing_reset()
+    for _ in range(breakdown_steps):
+        (g_stage.replay if g_stage is not None else step)()
+    torch.cuda.synchronize()
+    rp.rpca_timing_enable(False)
+    per = 1 if g_stage is not None else breakdown_steps     # a graph's events hold the last replay
+    try:
+        stage = {name: rp.rpca_timing_read(kind)[1] / per
+                 for name, kind in (("apply", 0), ("adjoint", 1), ("small_svd", 3), ("gram", 5), ("chol", 6),
+                                    ("trsm", 7), ("centre", 8), ("lift", 9))}
+    except Exception as e:                                      # noqa: BLE001
+        print(f"stage events unreadable ({e})", file=sys.stderr)
+        stage = None
+    rp.rpca_timing_reset()
+    del g_stage
 
     # roofline of the dominant kernel (the passes over A)
     pk = peaks()
@@ -1083,12 +1102,16 @@ def main():
                                       if args.precision == "bf16x3" else "passes over A in FP32 FFMA"),
                    "A_bytes": int(a_bytes), "l2": "A (%.0f MB) is larger than L2 (129 MB); no flush" % (a_bytes / 1e6),
                    "parallelism": f"replicas x{world}",
-                   "launch": ("one PCA captured as a CUDA graph and replayed per step; stage times from the "
-                              "last replay's events" if graph is not None else "eager launches")},
+                   "launch": ("one PCA captured as a CUDA graph and replayed per step; event pairs around the "
+                              "pass kernels only; their durations from the last replay" if graph is not None
+                              else "eager launches")},
         "gbs_per_pass": gbs_per_pass,
         "passes_per_step": passes / args.steps,
-        "stage_ms_per_step": dict({"apply": t_apply / args.steps, "adjoint": t_adj / args.steps,
-                                   "small_svd": t_svd / args.steps}, **extra),
+        "stage_ms_per_step": stage,
+        "stage_note": ("one fully instrumented replay after the timed region (event pairs around every "
+                       "stage); apply / adjoint include the BF16 split of the block operand"),
+        "pass_kernel_ms": {"apply": t_apply / max(n_apply, 1), "adjoint": t_adj / max(n_adj, 1),
+                           "launches_per_step": (n_apply + n_adj) / args.steps},
         "accuracy": {"resid_est": est, "resid_est_iters": args.resid_iters_conv, "sigma_k1": sk1,
                      "sigma_k1_from": sk1_how, "resid_over_sigma_k1": est / sk1,
                      "resid20_over_sigma_k1": est20 / sk1, "by_its": accuracy_by_its,

@@ -403,7 +403,9 @@ int64_t rpca_launch_count(void);
  * of each timed stage are bracketed by CUDA events on their stream:
  *   kind 0 = products A X (the sketch and the A half of each power iteration),
  *   kind 1 = adjoint products A^T Q (the A^* half and B^* = A_c^* Q),
- *   kind 3 = small SVD (Jacobi + rotation replay).
+ *   kind 3 = small SVD (Jacobi + rotation replay), 5 = Gram matrices,
+ *   6 = l x l Cholesky / LU factors, 7 = products with R^-1, 8 = centring,
+ *   9 = lifts U = Q W, V = Q2 Z.
  * rpca_timing_read waits for the recorded events and returns the number of
  * timed launches of `kind` since the last reset and their summed duration.
  * rpca_timing_enable(on): 0 = off, 1 = on, > 1 = on and create that many
@@ -411,6 +413,11 @@ int64_t rpca_launch_count(void);
  * Host-side state; not for use during CUDA graph capture.
  * ---------------------------------------------------------------------- */
 int rpca_timing_enable(int32_t on);
+/* Time only the kinds whose bit (1 << kind) is set in kinds_mask (default: all).
+ * Every timed stage adds two event records to the stream (or two event nodes to a
+ * captured graph), so a benchmark that times the whole PCA selects the few kinds
+ * it needs inside its timed window. */
+int rpca_timing_select(uint32_t kinds_mask);
 int rpca_timing_reset(void);
 int rpca_timing_read(int32_t kind, int64_t *count, double *total_ms);
 

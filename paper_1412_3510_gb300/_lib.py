@@ -81,6 +81,7 @@ SIGNATURES = [
     ("rpca_status_string", C.c_char_p, [C.c_int]),
     ("rpca_launch_count", C.c_int64, []),
     ("rpca_timing_enable", C.c_int, [_I32]),
+    ("rpca_timing_select", C.c_int, [C.c_uint32]),
     ("rpca_timing_reset", C.c_int, []),
     ("rpca_timing_read", C.c_int, [_I32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 ]

@@ -12,6 +12,7 @@
 // each heavy row's partials in chunk order.
 #include "pipeline.cuh"
 #include "resid.cuh"
+#include "timing.cuh"
 
 namespace rpca {
 
@@ -554,9 +555,15 @@ CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
 // A (CSR) and A^T (CSR, built by the stable sort) as the pipeline's operator.
 struct CsrOp final : Operator {
     Spmm a, t;
-    int apply(const float *X, int lp, float *Y, cudaStream_t s) const override { return a.run(X, lp, Y, s); }
+    int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *) const override {
+        TimedScope ts(kTimeApplyKernel, s);
+        return a.run(X, lp, Y, s);
+    }
     int adjoint_splits(int) const override { return 1; }
-    int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const override { return t.run(Q, lp, part, s); }
+    int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const override {
+        TimedScope ts(kTimeAdjointKernel, s);
+        return t.run(Q, lp, part, s);
+    }
 };
 
 // Build A^T from A and the SpMM plans of both, inside the scratch at `base`.

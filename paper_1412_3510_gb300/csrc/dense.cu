@@ -2,6 +2,7 @@
 #include "pipeline.cuh"
 #include "resid.cuh"
 #include "tc_gemm.cuh"
+#include "timing.cuh"
 
 namespace rpca {
 
@@ -20,14 +21,17 @@ struct DenseOp final : Operator {
         if (precision != RPCA_PREC_BF16X3) return 0;
         return std::max(tc_split_bytes(n, lp), tc_split_bytes(m, lp));
     }
-    int apply(const float *X, int lp, float *Y, cudaStream_t s) const override {
+    int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *bias) const override {
         if (tc(lp)) {
             auto *xs = reinterpret_cast<__nv_bfloat16 *>(scratch);
             RPCA_TRY(launch_tc_split(X, n, lp, xs, s));
-            return launch_tc_apply(A, m, n, lda, xs, lp, Y, st, s);
+            TimedScope ts(kTimeApplyKernel, s);
+            return launch_tc_apply(A, m, n, lda, xs, lp, Y, st, s, bias);
         }
-        return launch_sgemm(false, m, lp, n, A, lda, X, lp, Y, lp, 1, 0, s);
+        TimedScope ts(kTimeApplyKernel, s);
+        return launch_sgemm(false, m, lp, n, A, lda, X, lp, Y, lp, 1, 0, s, nullptr, bias);
     }
+    bool fuses_bias() const override { return true; }
     int adjoint_splits(int lp) const override {
         return tc(lp) ? tc_adjoint_splits(n, m, lp) : choose_splits(n, lp, m);
     }
@@ -36,8 +40,10 @@ struct DenseOp final : Operator {
         if (tc(lp)) {
             auto *qs = reinterpret_cast<__nv_bfloat16 *>(scratch);
             RPCA_TRY(launch_tc_split(Q, m, lp, qs, s));
+            TimedScope ts(kTimeAdjointKernel, s);
             return launch_tc_adjoint(A, m, n, lda, qs, lp, part, sp, st, s);
         }
+        TimedScope ts(kTimeAdjointKernel, s);
         return launch_sgemm(true, n, lp, m, A, lda, Q, lp, part, lp, sp, n * (int64_t)lp, s);
     }
 };
@@ -192,7 +198,7 @@ extern "C" int rpca_dense_pass(const float *A, int64_t m, int64_t n, int64_t lda
     op.st = reinterpret_cast<rpca::DevStatus *>(base + P.status);
     op.scratch = base + P.scratch;
     if (cudaMemsetAsync(op.st, 0, sizeof(rpca::DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
-    if (!adjoint) return op.apply(B, w, C, s);
+    if (!adjoint) return op.apply(B, w, C, s, nullptr);
     float *part = reinterpret_cast<float *>(base + P.part);
     RPCA_TRY(op.adjoint(B, w, part, s));
     return rpca::launch_adjoint_reduce(part, P.splits, n, w, w, C, 0, (double)m, nullptr, 0, s);

@@ -31,7 +31,8 @@ template <int BM, int BN, int TM, int TN, bool TRANS_A>
 __global__ void __launch_bounds__(kThreads)
 sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64_t lda,
              const float *__restrict__ B, int64_t ldb, float *__restrict__ C, int64_t ldc,
-             int64_t kchunk, int64_t split_stride, const int *__restrict__ copy_flag) {
+             int64_t kchunk, int64_t split_stride, const int *__restrict__ copy_flag,
+             const float *__restrict__ bias) {
     constexpr int BK = kBK;
     constexpr int TX = BN / TN;
     constexpr int TY = BM / TM;
@@ -189,6 +190,16 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64
         }
     }
 
+    if (!TRANS_A && bias) {
+        // implicit centring (Section 5): C = A B - 1 (c B), the row vector c B given
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t c = n0 + tx * TN + j;
+            const float bj = c < N ? bias[c] : 0.f;
+#pragma unroll
+            for (int i = 0; i < TM; ++i) acc[i][j] -= bj;
+        }
+    }
     const bool vecC = aligned16(C) && (ldc % 4 == 0) && (TN % 4 == 0);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -213,7 +224,7 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, const float *__restrict__ A, int64
 template <int BM, int BN, int TM, int TN>
 int launch_cfg(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-               int64_t split_stride, cudaStream_t s, const int *copy_flag) {
+               int64_t split_stride, cudaStream_t s, const int *copy_flag, const float *bias) {
     const int64_t kchunk = round_up(cdiv(K, splits), kBK);
     const int64_t gz = cdiv(K, kchunk);
     // slices past the end of K still write zero partials so the reduction sees `splits` slices
@@ -222,10 +233,10 @@ int launch_cfg(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, in
     if (grid.x > 2147483647u || grid.y > 65535u || grid.z > 65535u) return RPCA_ERR_INVALID_ARG;
     if (trans_a)
         sgemm_kernel<BM, BN, TM, TN, true><<<grid, kThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                                     kchunk, split_stride, nullptr);
+                                                                     kchunk, split_stride, nullptr, nullptr);
     else
         sgemm_kernel<BM, BN, TM, TN, false><<<grid, kThreads, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
-                                                                      kchunk, split_stride, copy_flag);
+                                                                      kchunk, split_stride, copy_flag, bias);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
@@ -251,7 +262,8 @@ template <int NG, int RPT>
 __global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int K, const float *__restrict__ A,
                                                           int64_t lda, const float *__restrict__ B, int64_t ldb,
                                                           float *__restrict__ C, int64_t ldc,
-                                                          const int *__restrict__ copy_flag) {
+                                                          const int *__restrict__ copy_flag,
+                                                          const float *__restrict__ bias) {
     extern __shared__ float sk[];
     constexpr int NB = 16 * NG;                  // B columns in shared memory
     constexpr int kRows = 16 * RPT;              // rows of A per CTA
@@ -300,14 +312,14 @@ __global__ void __launch_bounds__(256) smallk_gemm_kernel(int64_t M, int N, int 
 #pragma unroll
         for (int j = 0; j < NG; ++j) {
             const int c = tx + 16 * j;
-            if (c < N) C[r * ldc + c] = acc[i][j];
+            if (c < N) C[r * ldc + c] = bias ? acc[i][j] - bias[c] : acc[i][j];
         }
     }
 }
 
 template <int NG>
 int launch_smallk(int64_t M, int N, int K, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
-                  int64_t ldc, cudaStream_t s, const int *copy_flag) {
+                  int64_t ldc, cudaStream_t s, const int *copy_flag, const float *bias) {
     // 64-row tiles while they fill two waves of the SMs, 16-row tiles below that
     const bool short_block = cdiv(M, (int64_t)64) < 2LL * num_sms();
     const int rows = short_block ? 16 : 64;
@@ -315,35 +327,36 @@ int launch_smallk(int64_t M, int N, int K, const float *A, int64_t lda, const fl
     auto kern = short_block ? smallk_gemm_kernel<NG, 1> : smallk_gemm_kernel<NG, 4>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RPCA_ERR_CUDA;
-    kern<<<(unsigned)cdiv(M, (int64_t)rows), 256, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, copy_flag);
+    kern<<<(unsigned)cdiv(M, (int64_t)rows), 256, smem, s>>>(M, N, K, A, lda, B, ldb, C, ldc, copy_flag, bias);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
 
 int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                  const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-                 int64_t split_stride, cudaStream_t s, const int *copy_flag) {
+                 int64_t split_stride, cudaStream_t s, const int *copy_flag, const float *bias) {
     if (M <= 0 || N <= 0) return RPCA_OK;
+    if (bias && (trans_a || splits > 1)) return RPCA_ERR_INVALID_ARG;
     if (splits < 1) splits = 1;
     if (!trans_a && splits == 1 && K >= 1 && K <= 160 && N <= 160 && (!copy_flag || N == K)) {
         const int ng = (int)cdiv(N, (int64_t)16), n = (int)N, k = (int)K;
         switch (ng) {
-            case 1: return launch_smallk<1>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 2: return launch_smallk<2>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 3: return launch_smallk<3>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 4: return launch_smallk<4>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 5: return launch_smallk<5>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 6: return launch_smallk<6>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 7: return launch_smallk<7>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 8: return launch_smallk<8>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            case 9: return launch_smallk<9>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
-            default: return launch_smallk<10>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag);
+            case 1: return launch_smallk<1>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 2: return launch_smallk<2>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 3: return launch_smallk<3>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 4: return launch_smallk<4>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 5: return launch_smallk<5>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 6: return launch_smallk<6>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 7: return launch_smallk<7>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 8: return launch_smallk<8>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            case 9: return launch_smallk<9>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
+            default: return launch_smallk<10>(M, n, k, A, lda, B, ldb, C, ldc, s, copy_flag, bias);
         }
     }
-    if (N <= 16) return launch_cfg<128, 16, 4, 2>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
-    if (N <= 32) return launch_cfg<128, 32, 4, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
-    if (N <= 64) return launch_cfg<128, 64, 8, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
-    return launch_cfg<128, 128, 8, 8>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag);
+    if (N <= 16) return launch_cfg<128, 16, 4, 2>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag, bias);
+    if (N <= 32) return launch_cfg<128, 32, 4, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag, bias);
+    if (N <= 64) return launch_cfg<128, 64, 8, 4>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag, bias);
+    return launch_cfg<128, 128, 8, 8>(trans_a, M, N, K, A, lda, B, ldb, C, ldc, splits, split_stride, s, copy_flag, bias);
 }
 
 }  // namespace rpca

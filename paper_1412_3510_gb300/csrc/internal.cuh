@@ -70,10 +70,13 @@ int launch_omega(int64_t n, int l, uint64_t seed, uint64_t stream_id, const floa
 // slice z writes C + z * split_stride.  op(A) = A (A is M x K, lda) when
 // !trans_a, and A^T (A stored K x M, lda) when trans_a.  B is K x N (ldb).
 // When copy_flag is given and *copy_flag == 0 (read on the device), the
-// kernel copies C = A (non-transposed, M x N) instead of multiplying.
+// kernel copies C = A (non-transposed, M x N) instead of multiplying.  bias
+// (N values, non-transposed and unsplit only): C = A B - 1 bias, Section 5's
+// implicit centring with bias = c B.
 int launch_sgemm(bool trans_a, int64_t M, int64_t N, int64_t K, const float *A, int64_t lda,
                  const float *B, int64_t ldb, float *C, int64_t ldc, int splits,
-                 int64_t split_stride, cudaStream_t s, const int *copy_flag = nullptr);
+                 int64_t split_stride, cudaStream_t s, const int *copy_flag = nullptr,
+                 const float *bias = nullptr);
 
 // Partial Grams part[s] (lp x lp) = Y[chunk s]^T Y[chunk s] of a row-major Y
 // (rows x lp, ld = lp); skipped entirely when *skip_flag == 0.
@@ -115,9 +118,15 @@ int launch_gram_reduce(const float *part, int splits, int l, int lp, float *G, c
                        const int *skip_flag = nullptr);
 
 // X = sum_s part[s] (rows x lp); when centring, X[:, c] -= (X[:, l] / m) * qsum[c]
-// with qsum from the column-sum partials of Q; padding columns zeroed.
+// with qsum from the column-sum partials of Q; padding columns zeroed.  cvec
+// (optional, centring only): the column means of A, c[j] = X[j][l] / m.
 int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, int lp, float *X,
-                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s);
+                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s,
+                          float *cvec = nullptr);
+
+// bias[j] = sum_i c[i] X[i][j] for j < l, 0 for l <= j < lp (c: n values, X: n x lp):
+// the row vector c X of Section 5's implicit centring A*X - ones(m,1)*(c*X).
+int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *bias, cudaStream_t s);
 
 // One CTA: Cholesky G = R^T R in FP32 (shifted on breakdown), Rinv (lp x lp,
 // zero padded) = R^-1; optionally Racc_out = R * Racc_in (l x l, upper).

@@ -126,6 +126,8 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.rinv_m = take(lp * lp * 4);
     L.flags = take(256);
     L.scal = take(256);
+    L.cvec = take((size_t)n * 4);
+    L.bias = take(lp * 4);
     L.lu0 = take(tslu_ids_bytes(std::max(m, n), l));
     L.lu1 = take(tslu_ids_bytes(std::max(m, n), l));
     L.rsplit = take(tc_rmul_split_bytes(L.lp));
@@ -208,11 +210,11 @@ int cholqr_round(const Ctx &c, const float *in, float *out, int64_t rows, int sp
 // and kept, R^-1 goes to rinv_m for the next adjoint product (implicit Q).
 // Final: explicit orthonormal Q in y1 (CholeskyQR two or three times).
 // Returns through *q the block the next adjoint product reads.
-int renorm_m(const Ctx &c, bool raw, bool final_, const float **q, bool *pending) {
+int renorm_m(const Ctx &c, bool raw, bool final_, const float **q, bool *pending, bool centred = false) {
     const Layout &L = c.L;
     float *y0 = c.at<float>(L.y0), *y1 = c.at<float>(L.y1);
     int *flag = c.at<int>(L.flags);
-    if (!raw) {
+    if (!raw && !centred) {
         TimedScope ts(kTimeCentre, c.s);
         int nch = 0;
         RPCA_TRY(launch_colsum_partial(y0, L.m, L.l, L.lp, c.at<float>(L.cpart), &nch, c.s));
@@ -268,7 +270,7 @@ int adjoint_pass(const Operator &op, const Ctx &c, bool raw, const float *q, boo
     const int splits = op.adjoint_splits(L.lp);
     float *dst = pending ? c.at<float>(L.x1) : c.at<float>(L.x0);
     RPCA_TRY(launch_adjoint_reduce(part, std::max(splits, 1), L.n, L.l, L.lp, dst, raw ? 0 : 1, (double)L.m,
-                                   c.at<float>(L.qpart), L.cchunks, c.s));
+                                   c.at<float>(L.qpart), L.cchunks, c.s, c.at<float>(L.cvec)));
     if (pending) {
         TimedScope ts(kTimeTrsm, c.s);
         RPCA_TRY(launch_sgemm(false, L.n, L.lp, L.lp, dst, L.lp, c.at<float>(L.rinv_m), L.lp, c.at<float>(L.x0), L.lp,
@@ -302,21 +304,31 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
         RPCA_TRY(launch_omega(L.n, l, o->seed, 0, o->col_weights, x1, lp, s));
     }
 
-    auto apply = [&](const float *X) {
+    // Products with A.  Centring (Section 5: A*X - ones(m,1)*(c*X)): the sketch comes
+    // before any adjoint product, so its rows are centred on their own mean (the mean of
+    // the rows of A X is c X); after the first adjoint pass has produced c, the row
+    // vector c X is formed from the small block and subtracted in the product's epilogue.
+    const bool fuse = !raw && op.fuses_bias();
+    float *bias = c.at<float>(L.bias);
+    auto apply = [&](const float *X, bool with_bias) {
+        if (with_bias) {
+            TimedScope tc(kTimeCentre, s);
+            RPCA_TRY(launch_centring_row(c.at<float>(L.cvec), X, L.n, l, lp, bias, s));
+        }
         TimedScope ts(kTimeApply, s);
-        return op.apply(X, lp, y0, s);
+        return op.apply(X, lp, y0, s, with_bias ? bias : nullptr);
     };
     // sketch and power iterations; odd-only: the products with A^* (the even-numbered
     // ones) feed the next product with A unrenormalised (x0's padding columns are zero)
     const float *q = nullptr;
     bool pending = false;
-    RPCA_TRY(apply(x1));
+    RPCA_TRY(apply(x1, false));
     RPCA_TRY(renorm_m(c, raw, o->its == 0, &q, &pending));
     for (int it = 1; it <= o->its; ++it) {
         RPCA_TRY(adjoint_pass(op, c, raw, q, pending));
         if (!odd_only) RPCA_TRY(renorm_n(c, false));
-        RPCA_TRY(apply(odd_only ? x0 : x1));
-        RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending));
+        RPCA_TRY(apply(odd_only ? x0 : x1, fuse));
+        RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending, fuse));
     }
 
     // B^* = A_c^* Q (Eq. i2), B^* = Q2 R, SVD of R^T (Eq. i3)
@@ -366,7 +378,7 @@ int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, i
     }
     auto apply = [&](const float *X, float *Y) {
         TimedScope ts(kTimeApply, s);
-        return op.apply(X, lp, Y, s);
+        return op.apply(X, lp, Y, s, nullptr);
     };
     const float *cur = x1;
     for (int it = 1; it <= o->its; ++it) {

@@ -12,8 +12,10 @@ struct Operator {
     DevStatus *st = nullptr;          // device status block
     virtual ~Operator() = default;
     virtual size_t scratch_bytes(int lp) const { (void)lp; return 0; }
-    // Y (m x lp) = A X (X n x lp); padding columns of X are zero.
-    virtual int apply(const float *X, int lp, float *Y, cudaStream_t s) const = 0;
+    // Y (m x lp) = A X (X n x lp); padding columns of X are zero.  bias (lp values,
+    // only when fuses_bias()): Y = A X - 1 bias, the implicit centring.
+    virtual int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *bias = nullptr) const = 0;
+    virtual bool fuses_bias() const { return false; }
     // part / X: X (n x lp) = A^T Q as `splits` partial slices in `part`
     // (n x lp each), or written directly when splits() == 0.
     virtual int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const = 0;
@@ -26,7 +28,8 @@ struct Layout {
     int s_adj = 0, s_gram_m = 0, s_gram_n = 0, cchunks = 0;
     size_t status = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, part = 0, cpart = 0, qpart = 0, G = 0,
            rinv = 0, racc0 = 0, racc1 = 0, wk = 0, zk = 0, sig = 0, perm = 0, rot = 0, zbuf = 0,
-           rinv_m = 0, flags = 0, scal = 0, lu0 = 0, lu1 = 0, rsplit = 0, scratch = 0, total = 0;
+           rinv_m = 0, flags = 0, scal = 0, cvec = 0, bias = 0, lu0 = 0, lu1 = 0, rsplit = 0, scratch = 0,
+           total = 0;
 };
 
 Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_t op_scratch);

@@ -143,7 +143,7 @@ gram_reduce_kernel(const float *__restrict__ part, int splits, int l, int lp, fl
 __global__ void __launch_bounds__(256)
 adjoint_reduce_kernel(const float *__restrict__ part, int splits, int64_t rows, int l, int lp,
                       float *__restrict__ X, int centre, float inv_m,
-                      const float *__restrict__ qpart, int qchunks) {
+                      const float *__restrict__ qpart, int qchunks, float *__restrict__ cvec) {
     __shared__ float qsum[RPCA_MAX_L];
     if (centre) {
         for (int c = threadIdx.x; c < l; c += blockDim.x) {
@@ -167,6 +167,7 @@ adjoint_reduce_kernel(const float *__restrict__ part, int splits, int64_t rows, 
             float s = 0.f;
             for (int q = 0; q < splits; ++q) s += p[q * stride + l];
             cj = s * inv_m;
+            if (cvec && threadIdx.x == 0) cvec[j] = cj;
         }
         for (int c = threadIdx.x; c < lp; c += blockDim.x) {
             float v = 0.f;
@@ -182,6 +183,37 @@ adjoint_reduce_kernel(const float *__restrict__ part, int splits, int64_t rows, 
             }
             X[j * lp + c] = v;
         }
+    }
+}
+
+// bias[j] = sum_i c[i] X[i][j] (j < l), 0 for l <= j < lp.  A CTA owns 32 columns
+// (threadIdx.x) with eight interleaved row groups (threadIdx.y), each a compensated
+// sum; the eight group sums are combined in order (deterministic).
+__global__ void __launch_bounds__(256)
+centring_row_kernel(const float *__restrict__ c, const float *__restrict__ X, int64_t n, int l, int lp,
+                    float *__restrict__ bias) {
+    __shared__ float sh[8][32], ch[8][32];
+    const int j = blockIdx.x * 32 + threadIdx.x, y = threadIdx.y;
+    float s = 0.f, comp = 0.f;
+    if (j < l)
+        for (int64_t i = y; i < n; i += 8) {
+            const float v = c[i] * X[i * lp + j] - comp;
+            const float t = s + v;
+            comp = (t - s) - v;
+            s = t;
+        }
+    sh[y][threadIdx.x] = s;
+    ch[y][threadIdx.x] = comp;
+    __syncthreads();
+    if (y == 0 && j < lp) {
+        float t = 0.f, cc = 0.f;
+        for (int g = 0; g < 8; ++g) {
+            const float v = (sh[g][threadIdx.x] - ch[g][threadIdx.x]) - cc;
+            const float u = t + v;
+            cc = (u - t) - v;
+            t = u;
+        }
+        bias[j] = j < l ? t : 0.f;
     }
 }
 
@@ -231,11 +263,17 @@ int launch_gram_reduce(const float *part, int splits, int l, int lp, float *G, c
 }
 
 int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, int lp, float *X,
-                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s) {
+                          int centre, double m, const float *qpart, int qchunks, cudaStream_t s, float *cvec) {
     dim3 block(32, 8);
     const int64_t grid = std::min<int64_t>(cdiv(rows, 8), (int64_t)num_sms() * 8);
     adjoint_reduce_kernel<<<(unsigned)std::max<int64_t>(grid, 1), block, 0, s>>>(
-        part, splits, rows, l, lp, X, centre, (float)(1.0 / m), qpart, qchunks);
+        part, splits, rows, l, lp, X, centre, (float)(1.0 / m), qpart, qchunks, centre ? cvec : nullptr);
+    RPCA_CHECK_LAUNCH();
+    return RPCA_OK;
+}
+
+int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *bias, cudaStream_t s) {
+    centring_row_kernel<<<(unsigned)cdiv(lp, 32), dim3(32, 8), 0, s>>>(c, X, n, l, lp, bias);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

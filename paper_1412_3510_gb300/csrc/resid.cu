@@ -209,7 +209,7 @@ int run_resid(const Operator &op, int raw, const float *U, int64_t ldu, const fl
             wcolsum_kernel<<<R.nchunks, 256, 0, s>>>(V, n, k, ldv, x8, kW, tpart);
             RPCA_CHECK_LAUNCH();
         }
-        RPCA_TRY(op.apply(x8, kW, w8, s));
+        RPCA_TRY(op.apply(x8, kW, w8, s, nullptr));
         int wch = 0;
         if (centre) RPCA_TRY(launch_colsum_partial(w8, m, 1, kW, wpart, &wch, s));
         combine_m_kernel<<<R.mchunks, 256, 0, s>>>(w8, m, wpart, wch, centre, U, ldu, S, tpart,

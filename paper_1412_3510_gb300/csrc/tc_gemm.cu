@@ -83,6 +83,7 @@ struct TcArgs {
     DevStatus *st;
     int chunk_st;                 // K stages per TMEM accumulation chain
     const int *skip;              // optional: the launch does nothing when *skip == 0
+    const float *bias;            // optional (A X only): out = A X - 1 bias (implicit centring)
 };
 
 constexpr int kThreads = 512;     // 16 warps
@@ -265,6 +266,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 } else {
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                }
+                if (!ADJ && args.bias && ch == 0) {
+                    // Section 5's implicit centring A*X - ones(m,1)*(c*X), bias = c X
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (c0 + e < args.ncols_store) v[e] -= args.bias[c0 + e];
                 }
                 if (live) {
                     // chunk 0 stores; later chunks of the tile add in FP32 (round to nearest)
@@ -505,12 +512,12 @@ int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cu
 }
 
 int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *xsplit, int lp,
-                    float *Y, DevStatus *st, cudaStream_t s) {
+                    float *Y, DevStatus *st, cudaStream_t s, const float *bias) {
     const int N = tc_n(lp), BK = tc_bk(lp);
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
     const int tiles = (int)cdiv(m, kBM);
-    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK), nullptr};
+    TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK), nullptr, bias};
     dim3 grid((unsigned)std::min(tiles, num_sms()), 1, 1);
     return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
 }

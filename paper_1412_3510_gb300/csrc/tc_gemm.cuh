@@ -15,9 +15,9 @@ int tc_adjoint_splits(int64_t n, int64_t m, int lp);
 
 // FP32 block P (rows x lp) -> BF16 hi/lo per stage in the MMA's K-major layout.
 int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cudaStream_t s);
-// Y (m x lp) = A X, X given pre-split.
+// Y (m x lp) = A X, X given pre-split; with bias (lp values), Y = A X - 1 bias.
 int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *xsplit, int lp,
-                    float *Y, DevStatus *st, cudaStream_t s);
+                    float *Y, DevStatus *st, cudaStream_t s, const float *bias = nullptr);
 // part[s] (n x lp) = A^T Q over the rows of split s, Q given pre-split.
 int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *qsplit, int lp,
                       float *part, int splits, DevStatus *st, cudaStream_t s);

@@ -15,6 +15,7 @@ struct Rec { int kind; cudaEvent_t a, b; };
 
 std::mutex g_mu;
 bool g_on = false;
+uint32_t g_mask = 0xffffffffu;     // kinds that record events
 std::vector<Rec> g_recs;       // recorded in the current window
 std::vector<cudaEvent_t> g_pool;
 
@@ -40,7 +41,7 @@ void record(cudaEvent_t e, cudaStream_t s) {
 bool timing_on() { return g_on; }
 
 TimedScope::TimedScope(int kind, cudaStream_t s) : kind_(kind), s_(s) {
-    if (!g_on) return;
+    if (!g_on || kind < 0 || kind > 31 || !((g_mask >> kind) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     a_ = take_event();
     b_ = take_event();
@@ -65,6 +66,12 @@ extern "C" int rpca_timing_enable(int32_t on) {
         if (cudaEventCreate(&e) != cudaSuccess) return RPCA_ERR_CUDA;
         rpca::g_pool.push_back(e);
     }
+    return RPCA_OK;
+}
+
+extern "C" int rpca_timing_select(uint32_t kinds_mask) {
+    std::lock_guard<std::mutex> lk(rpca::g_mu);
+    rpca::g_mask = kinds_mask;
     return RPCA_OK;
 }
 

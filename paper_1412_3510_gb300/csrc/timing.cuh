@@ -7,7 +7,8 @@ namespace rpca {
 
 enum TimedKind {
     kTimeApply = 0, kTimeAdjoint = 1, kTimeRenorm = 2, kTimeSmallSvd = 3, kTimeResid = 4,
-    kTimeGram = 5, kTimeChol = 6, kTimeTrsm = 7, kTimeCentre = 8, kTimeLift = 9
+    kTimeGram = 5, kTimeChol = 6, kTimeTrsm = 7, kTimeCentre = 8, kTimeLift = 9,
+    kTimeApplyKernel = 10, kTimeAdjointKernel = 11     // the pass kernel alone (no operand split)
 };
 
 bool timing_on();

@@ -238,6 +238,12 @@ def rpca_timing_enable(on: bool = True, reserve: int = 0) -> None:
     _check(L.load().rpca_timing_enable(max(int(bool(on)), int(reserve) if on else 0)), "rpca_timing_enable")
 
 
+def rpca_timing_select(kinds=None) -> None:
+    """Time only the given stage kinds (None: all)."""
+    mask = 0xFFFFFFFF if kinds is None else sum(1 << int(k) for k in kinds)
+    _check(L.load().rpca_timing_select(mask), "rpca_timing_select")
+
+
 def rpca_timing_reset() -> None:
     _check(L.load().rpca_timing_reset(), "rpca_timing_reset")
 
