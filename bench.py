@@ -903,8 +903,9 @@ def main():
     rp.rpca_timing_select(None)
     breakdown_steps = 3
     rp.rpca_timing_enable(True, reserve=2 * (12 * its + 40) * breakdown_steps + 64)
-    g_stage = capture_graph(rp, step)[0] if graph is not None else None
     rp.rpca_timing_reset()
+    # the captured graph's event nodes are the records read below (each replay re-records them)
+    g_stage = capture_graph(rp, step)[0] if graph is not None else None
     for _ in range(breakdown_steps):
         (g_stage.replay if g_stage is not None else step)()
     torch.cuda.synchronize()

@@ -32,6 +32,9 @@ struct DenseOp final : Operator {
         return launch_sgemm(false, m, lp, n, A, lda, X, lp, Y, lp, 1, 0, s, nullptr, bias);
     }
     bool fuses_bias() const override { return true; }
+    // the tensor cores' FP32 accumulation drifts (about 2^-27 per K element, chunked at
+    // 2048), which puts up to ~1e-5 relative error into the column means c = A^T 1 / m
+    bool exact_bias(int lp) const override { return !tc(lp); }
     int adjoint_splits(int lp) const override {
         return tc(lp) ? tc_adjoint_splits(n, m, lp) : choose_splits(n, lp, m);
     }

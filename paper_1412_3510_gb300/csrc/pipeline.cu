@@ -327,8 +327,12 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     for (int it = 1; it <= o->its; ++it) {
         RPCA_TRY(adjoint_pass(op, c, raw, q, pending));
         if (!odd_only) RPCA_TRY(renorm_n(c, false));
-        RPCA_TRY(apply(odd_only ? x0 : x1, fuse));
-        RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending, fuse));
+        // the block that becomes the final Q is centred on its own row mean unless the
+        // bias matches the product exactly (intermediate blocks reach the output only
+        // through A_c^*, which annihilates the ones direction)
+        const bool with_bias = fuse && (it < o->its || op.exact_bias(lp));
+        RPCA_TRY(apply(odd_only ? x0 : x1, with_bias));
+        RPCA_TRY(renorm_m(c, raw, it == o->its, &q, &pending, with_bias));
     }
 
     // B^* = A_c^* Q (Eq. i2), B^* = Q2 R, SVD of R^T (Eq. i3)

@@ -16,6 +16,11 @@ struct Operator {
     // only when fuses_bias()): Y = A X - 1 bias, the implicit centring.
     virtual int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *bias = nullptr) const = 0;
     virtual bool fuses_bias() const { return false; }
+    // True when the bias c X matches the product's own row mean to FP32 rounding (the
+    // column means come from an FP32-accumulated adjoint product).  Otherwise the
+    // block that becomes the final Q, whose ones-direction component reaches U
+    // unfiltered, is centred on its own row mean instead.
+    virtual bool exact_bias(int lp) const { (void)lp; return false; }
     // part / X: X (n x lp) = A^T Q as `splits` partial slices in `part`
     // (n x lp each), or written directly when splits() == 0.
     virtual int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const = 0;
