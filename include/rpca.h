@@ -64,8 +64,14 @@ typedef enum rpca_status {
  * BF16 pieces (exact) with the six products of order <= 2^-18: FP32 accuracy. */
 typedef enum rpca_precision {
     RPCA_PREC_FP32 = 0,          /* passes over A in FP32 FFMA (the plain form) */
-    RPCA_PREC_BF16X3 = 1         /* passes over A on tcgen05 tensor cores: a = a_hi + a_lo
+    RPCA_PREC_BF16X3 = 1,        /* passes over A on tcgen05 tensor cores: a = a_hi + a_lo
                                     in BF16, three products accumulated in FP32 (TMEM) */
+    /* Flag, or'ed into either form: the l x l work in FP64 -- the Cholesky factors and
+     * triangular inverses of the CholeskyQR renormalisations, the accumulated factor R
+     * of B^* = Q2 R, and the SVD of R^T (FP32 Jacobi refined to FP64 accuracy).  The
+     * Gram matrices stay compensated FP32 and the LU renormalisation FP32.  Not for
+     * rpca_batched or rpca_dense_pass (RPCA_ERR_UNSUPPORTED / RPCA_ERR_INVALID_ARG). */
+    RPCA_PREC_SMALL_FP64 = 16
 } rpca_precision;
 
 typedef enum rpca_renorm {
@@ -383,6 +389,19 @@ int rpca_dense_learned(const float *A, int64_t m, int64_t n, int64_t lda, const 
  * ---------------------------------------------------------------------- */
 int rpca_gaussian_omega(int64_t n, int32_t l, uint64_t seed, uint64_t stream_id,
                         float *omega, int64_t ldo, rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * The SVD of the small factor alone (Eq. i3), as the method runs it with
+ * RPCA_PREC_SMALL_FP64: M = W diag(S) Z^T for an l x l M (FP64, row-major,
+ * device; l <= RPCA_MAX_L), by FP32 one-sided Jacobi refined to FP64 accuracy.
+ * S: l values, descending; W, Z: l x l (FP64, row-major, columns = singular
+ * vectors).  Singular values closer than 2^-20 relative are left at FP32
+ * accuracy (the refinement does not separate such pairs).  For tests of that step.
+ * ws: rpca_small_svd_workspace_size(l) bytes, 256-byte aligned.
+ * ---------------------------------------------------------------------- */
+size_t rpca_small_svd_workspace_size(int32_t l);
+int rpca_small_svd(const double *M, int32_t l, double *S, double *W, double *Z, void *ws, size_t ws_bytes,
+                   rpca_stream_t stream);
 
 /* Raw Philox4x64-10 words: out[4 b + w] = word w of block (counter (first + b, 0, 0, 0),
  * key (key0, key1)) for b < nblocks (device output). */

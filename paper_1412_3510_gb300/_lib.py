@@ -26,6 +26,7 @@ RPCA_MLP_PACKED_BYTES = 38416
 PREC = {"fp32": 0, "bf16x3": 1}
 RENORM = {"cholqr": 0, "lu": 1}
 RPCA_RENORM_ODD_ONLY = 4
+RPCA_PREC_SMALL_FP64 = 16
 
 
 class RpcaOpts(C.Structure):
@@ -75,6 +76,8 @@ SIGNATURES = [
     ("rpca_dense_learned_workspace_size", _SZ, [_I64, _I64, _OPTS]),
     ("rpca_dense_learned", C.c_int, [_P, _I64, _I64, _I64, _OPTS, _P, _I32, C.c_double, _P, _I64, _P, _P, _I64,
                                      C.POINTER(C.c_double), _P, _SZ, _P]),
+    ("rpca_small_svd_workspace_size", _SZ, [_I32]),
+    ("rpca_small_svd", C.c_int, [_P, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),

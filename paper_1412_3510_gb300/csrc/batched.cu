@@ -109,7 +109,7 @@ int check_args(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t
     if (!o || count < 0 || (count > 0 && !descs) || o->l < 1 || o->l > 32 || o->k < 1 || o->k > o->l || o->its < 0 ||
         o->its > 1000 || max_m < 1 || max_n < 1 || count > 65536)
         return RPCA_ERR_INVALID_ARG;
-    if (o->omega || o->renorm != RPCA_RENORM_CHOLQR) return RPCA_ERR_UNSUPPORTED;
+    if (o->omega || o->renorm != RPCA_RENORM_CHOLQR || rpca::small_fp64(o->precision)) return RPCA_ERR_UNSUPPORTED;
     const size_t need = rpca_batched_workspace_size(count, max_m, max_n, o);
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
     return RPCA_OK;

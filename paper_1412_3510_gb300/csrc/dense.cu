@@ -62,7 +62,7 @@ extern "C" size_t rpca_dense_workspace_size(int64_t m, int64_t n, const rpca_opt
     // same workspace serves either precision
     const int splits = std::max(rpca::choose_splits(n, lp, m), rpca::tc_adjoint_splits(n, m, lp));
     rpca::DenseOp op;
-    op.m = m; op.n = n; op.precision = o->precision;
+    op.m = m; op.n = n; op.precision = rpca::pass_precision(o->precision);
     return rpca::make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp)).total;
 }
 
@@ -74,7 +74,7 @@ extern "C" int rpca_dense(const float *A, int64_t m, int64_t n, int64_t lda, con
     RPCA_TRY(rpca::check_common(m, n, o, U, ldu, S, V, ldv, ws, ws_bytes, need));
     if (rpca::renorm_kind(o->renorm) == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
     rpca::DenseOp op;
-    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
+    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = rpca::pass_precision(o->precision);
     const int lp = rpca::padded_l(o->l);
     const int splits = std::max(rpca::choose_splits(n, lp, m), rpca::tc_adjoint_splits(n, m, lp));
     const rpca::Layout L = rpca::make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp));
@@ -97,7 +97,7 @@ int run_sym(const float *A, int64_t n, int64_t lda, const rpca_opts *o, bool nys
             float *S, float *V, int64_t ldv, void *ws, rpca_stream_t stream) {
     if (rpca::renorm_kind(o->renorm) == RPCA_RENORM_LU && !rpca::tslu_supported(o->l)) return RPCA_ERR_UNSUPPORTED;
     rpca::DenseOp op;
-    op.m = n; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
+    op.m = n; op.n = n; op.A = A; op.lda = lda; op.precision = rpca::pass_precision(o->precision);
     const int lp = rpca::padded_l(o->l);
     const int splits = std::max(rpca::choose_splits(n, lp, n), rpca::tc_adjoint_splits(n, n, lp));
     const rpca::Layout L = rpca::make_layout(n, n, o->l, o->k, splits, op.scratch_bytes(lp));
@@ -127,7 +127,7 @@ namespace rpca {
 // small SVD (descending), valid after rpca_dense has run with the same arguments.
 size_t dense_sigma_offset(int64_t m, int64_t n, const float *A, int64_t lda, const rpca_opts *o) {
     DenseOp op;
-    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = o->precision;
+    op.m = m; op.n = n; op.A = A; op.lda = lda; op.precision = rpca::pass_precision(o->precision);
     const int lp = padded_l(o->l);
     const int splits = std::max(choose_splits(n, lp, m), tc_adjoint_splits(n, m, lp));
     return make_layout(m, n, o->l, o->k, splits, op.scratch_bytes(lp)).sig;

@@ -55,6 +55,10 @@ __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(
 // carries the column sums of A through the adjoint products), multiple of 8.
 static inline int padded_l(int l) { return (int)round_up(l + 1, 8); }
 
+// The precision of the passes over A, and the FP64 modifier of the l x l work.
+static inline int pass_precision(int p) { return p & ~RPCA_PREC_SMALL_FP64; }
+static inline bool small_fp64(int p) { return (p & RPCA_PREC_SMALL_FP64) != 0; }
+
 int num_sms();
 
 // ---------------------------------------------------------------------------
@@ -125,8 +129,11 @@ int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, in
                           float *cvec = nullptr);
 
 // bias[j] = sum_i c[i] X[i][j] for j < l, 0 for l <= j < lp (c: n values, X: n x lp):
-// the row vector c X of Section 5's implicit centring A*X - ones(m,1)*(c*X).
-int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *bias, cudaStream_t s);
+// the row vector c X of Section 5's implicit centring A*X - ones(m,1)*(c*X).  part:
+// centring_parts(n) x lp floats of scratch.
+int centring_parts(int64_t n);
+int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *part, float *bias,
+                        cudaStream_t s);
 
 // One CTA: Cholesky G = R^T R in FP32 (shifted on breakdown), Rinv (lp x lp,
 // zero padded) = R^-1; optionally Racc_out = R * Racc_in (l x l, upper).
@@ -136,6 +143,19 @@ int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp
 int launch_chol_inv(const float *G, int l, int lp, float *Rinv, const float *Racc_in,
                     float *Racc_out, DevStatus *st, cudaStream_t s, int *shifted_out = nullptr,
                     const int *skip_flag = nullptr);
+
+// The same factorisation in FP64 (RPCA_PREC_SMALL_FP64): Racc_in / Racc_out are l x l
+// FP64; Rinv is FP32 for the tall products.
+int launch_chol64(const float *G, int l, int lp, float *Rinv, const double *Racc_in, double *Racc_out, DevStatus *st,
+                  cudaStream_t s, int *shifted_out = nullptr, const int *skip_flag = nullptr);
+
+// Small SVD of R^T to FP64 accuracy: the FP32 Jacobi below on an FP32 copy of R, then
+// FP64 refinement.  r32 (l x l floats), wfull and zfull (lp x gram_ld(l) floats each) and
+// scratch (small_svd64_doubles(l) doubles) are workspace; outputs as launch_small_svd.
+size_t small_svd64_doubles(int l);
+int launch_small_svd64(const double *R, int l, int lp, int k, int kp, float *Wk, float *Zk, float *sig, float *rot,
+                       float *zbuf, int *perm, float *r32, float *wfull, float *zfull, double *scratch, DevStatus *st,
+                       cudaStream_t s, double *sig_d = nullptr, double *W_d = nullptr, double *Z_d = nullptr);
 
 // Small SVD of R^T (R = Racc, l x l upper): writes Wk (lp x kp, U-side
 // factors, k leading left singular vectors of R^T), sig (l, descending) and

@@ -49,7 +49,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // (the identity shift of the Nystrom method).  One CTA.
 __global__ void __launch_bounds__(256)
 symmetrize_kernel(const float *__restrict__ G, int l, int ldg, float *__restrict__ out, int ldo, float nu_scale,
-                  float *__restrict__ nu_out) {
+                  float *__restrict__ nu_out, double *__restrict__ out64 = nullptr) {
     __shared__ float red[256];
     float nu = 0.f;
     if (nu_out) {
@@ -68,7 +68,8 @@ symmetrize_kernel(const float *__restrict__ G, int l, int ldg, float *__restrict
         const int i = e / ldo, j = e - i * ldo;
         float v = 0.f;
         if (i < l && j < l) v = 0.5f * (G[(size_t)i * ldg + j] + G[(size_t)j * ldg + i]) + (i == j ? nu : 0.f);
-        out[e] = v;
+        if (out64) out64[e] = (double)v;
+        else out[e] = v;
     }
 }
 
@@ -115,8 +116,13 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.qpart = take((size_t)L.cchunks * l * 4);
     L.G = take((size_t)gram_ld(l) * gram_ld(l) * 4);
     L.rinv = take(lp * lp * 4);
-    L.racc0 = take((size_t)l * l * 4);
-    L.racc1 = take((size_t)l * l * 4);
+    // room for FP64 factors (RPCA_PREC_SMALL_FP64)
+    L.racc0 = take((size_t)l * l * 8);
+    L.racc1 = take((size_t)l * l * 8);
+    L.r32 = take((size_t)l * l * 4);
+    L.wfull = take(lp * gram_ld(l) * 4);
+    L.zfull = take(lp * gram_ld(l) * 4);
+    L.svd64 = take(small_svd64_doubles(l) * 8);
     L.wk = take(lp * L.kp * 4);
     L.zk = take(lp * L.kp * 4);
     L.sig = take(lp * 4);
@@ -128,6 +134,7 @@ Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_
     L.scal = take(256);
     L.cvec = take((size_t)n * 4);
     L.bias = take(lp * 4);
+    L.bpart = take((size_t)centring_parts(n) * lp * 4);
     L.lu0 = take(tslu_ids_bytes(std::max(m, n), l));
     L.lu1 = take(tslu_ids_bytes(std::max(m, n), l));
     L.rsplit = take(tc_rmul_split_bytes(L.lp));
@@ -144,7 +151,7 @@ int check_common(int64_t m, int64_t n, const rpca_opts *o, const float *U, int64
     if (o->k < 1 || o->l < o->k || o->l > RPCA_MAX_L || (int64_t)o->l > std::min(m, n)) return RPCA_ERR_INVALID_ARG;
     if (o->its < 0 || o->its > 1000) return RPCA_ERR_INVALID_ARG;
     if (ldu < o->k || ldv < o->k) return RPCA_ERR_INVALID_ARG;
-    if (o->precision != RPCA_PREC_FP32 && o->precision != RPCA_PREC_BF16X3) return RPCA_ERR_INVALID_ARG;
+    if ((o->precision & ~(RPCA_PREC_BF16X3 | RPCA_PREC_SMALL_FP64)) != 0) return RPCA_ERR_INVALID_ARG;
     if (renorm_kind(o->renorm) != RPCA_RENORM_CHOLQR && renorm_kind(o->renorm) != RPCA_RENORM_LU)
         return RPCA_ERR_INVALID_ARG;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < need) return RPCA_ERR_WORKSPACE;
@@ -159,8 +166,30 @@ struct Ctx {
     cudaStream_t s;
     DevStatus *st;
     bool lu = false;          // non-final renormalisations by tall-skinny LU
+    bool fp64 = false;        // l x l work in FP64 (the accumulated factors are doubles)
     template <class T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
 };
+
+// Cholesky + inverse (+ accumulated factor) of a reduced Gram matrix, FP32 or FP64.
+int chol_step(const Ctx &c, const float *G, float *rinv, const void *racc_in, void *racc_out, int *shifted_out,
+              const int *skip) {
+    if (c.fp64)
+        return launch_chol64(G, c.L.l, c.L.lp, rinv, static_cast<const double *>(racc_in),
+                             static_cast<double *>(racc_out), c.st, c.s, shifted_out, skip);
+    return launch_chol_inv(G, c.L.l, c.L.lp, rinv, static_cast<const float *>(racc_in), static_cast<float *>(racc_out),
+                           c.st, c.s, shifted_out, skip);
+}
+
+// SVD of R^T for the accumulated factor in racc0 (FP32 or FP64).
+int small_svd_step(const Ctx &c, float *wk, float *zk, float *sig) {
+    const Layout &L = c.L;
+    if (c.fp64)
+        return launch_small_svd64(c.at<double>(L.racc0), L.l, L.lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
+                                  c.at<float>(L.zbuf), c.at<int>(L.perm), c.at<float>(L.r32), c.at<float>(L.wfull),
+                                  c.at<float>(L.zfull), c.at<double>(L.svd64), c.st, c.s);
+    return launch_small_svd(c.at<float>(L.racc0), L.l, L.lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
+                            c.at<float>(L.zbuf), c.at<int>(L.perm), c.st, c.s);
+}
 
 // Gram, reduction and Cholesky of a tall block: rinv = R^-1 with in^T in = R^T R.
 int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *rinv, const float *racc_in,
@@ -179,7 +208,7 @@ int gram_chol(const Ctx &c, const float *in, int64_t rows, int splits, float *ri
         RPCA_TRY(launch_gram_reduce(part, splits, L.l, lp, G, c.s, skip));
     }
     TimedScope ts(kTimeChol, c.s);
-    return launch_chol_inv(G, L.l, lp, rinv, racc_in, racc_out, c.st, c.s, shifted_out, skip);
+    return chol_step(c, G, rinv, racc_in, racc_out, shifted_out, skip);
 }
 
 // Tall-skinny LU of a block: rinv = U^-1 with in = P^T L U (tournament pivoting).
@@ -284,7 +313,7 @@ int adjoint_pass(const Operator &op, const Ctx &c, bool raw, const float *q, boo
 int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float *S, float *V,
                  int64_t ldv, void *ws, const Layout &L, cudaStream_t s, bool clear_status) {
     Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status),
-          renorm_kind(o->renorm) == RPCA_RENORM_LU};
+          renorm_kind(o->renorm) == RPCA_RENORM_LU, small_fp64(o->precision)};
     op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
     op.st = c.st;
     const bool raw = o->raw != 0;
@@ -313,7 +342,7 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     auto apply = [&](const float *X, bool with_bias) {
         if (with_bias) {
             TimedScope tc(kTimeCentre, s);
-            RPCA_TRY(launch_centring_row(c.at<float>(L.cvec), X, L.n, l, lp, bias, s));
+            RPCA_TRY(launch_centring_row(c.at<float>(L.cvec), X, L.n, l, lp, c.at<float>(L.bpart), bias, s));
         }
         TimedScope ts(kTimeApply, s);
         return op.apply(X, lp, y0, s, with_bias ? bias : nullptr);
@@ -341,8 +370,7 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
     float *wk = c.at<float>(L.wk), *zk = c.at<float>(L.zk), *sig = c.at<float>(L.sig);
     {
         TimedScope ts(kTimeSmallSvd, s);
-        RPCA_TRY(launch_small_svd(c.at<float>(L.racc0), l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot),
-                                  c.at<float>(L.zbuf), c.at<int>(L.perm), c.st, s));
+        RPCA_TRY(small_svd_step(c, wk, zk, sig));
     }
 
     // V = Q2 Z_k, signs, U = Q W_k (Eq. i4)
@@ -363,7 +391,7 @@ int run_pipeline(Operator &op, const rpca_opts *o, float *U, int64_t ldu, float 
 int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, int64_t ldu, float *S, float *V,
                      int64_t ldv, void *ws, const Layout &L, cudaStream_t s) {
     Ctx c{L, reinterpret_cast<char *>(ws), s, reinterpret_cast<DevStatus *>(reinterpret_cast<char *>(ws) + L.status),
-          renorm_kind(o->renorm) == RPCA_RENORM_LU};
+          renorm_kind(o->renorm) == RPCA_RENORM_LU, small_fp64(o->precision)};
     op.scratch = reinterpret_cast<char *>(ws) + L.scratch;
     op.st = c.st;
     const bool odd_only = renorm_odd_only(o->renorm);
@@ -422,12 +450,12 @@ int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, i
     float *racc0 = c.at<float>(L.racc0);
     if (!nystrom) {
         // symmetric B = W Sigma Z^T (Jacobi); U = Q W, V = Q Z (Eqs. i3, i4 with B = Q^T A Q)
-        symmetrize_kernel<<<1, 256, 0, s>>>(G, l, gram_ld(l), racc0, l, 0.f, nullptr);
+        symmetrize_kernel<<<1, 256, 0, s>>>(G, l, gram_ld(l), racc0, l, 0.f, nullptr,
+                                            c.fp64 ? c.at<double>(L.racc0) : nullptr);
         RPCA_CHECK_LAUNCH();
         {
             TimedScope ts(kTimeSmallSvd, s);
-            RPCA_TRY(launch_small_svd(racc0, l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot), c.at<float>(L.zbuf),
-                                      c.at<int>(L.perm), c.st, s));
+            RPCA_TRY(small_svd_step(c, wk, zk, sig));
         }
         TimedScope ts_lift(kTimeLift, s);
         RPCA_TRY(launch_sgemm(false, n, L.k, lp, y1, lp, zk, L.kp, V, ldv, 1, 0, s));
@@ -451,7 +479,7 @@ int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, i
     float *rinv = c.at<float>(L.rinv);
     {
         TimedScope ts(kTimeChol, s);
-        RPCA_TRY(launch_chol_inv(B2, l, lp, rinv, nullptr, nullptr, c.st, s));
+        RPCA_TRY(chol_step(c, B2, rinv, nullptr, nullptr, nullptr, nullptr));
     }
     {
         TimedScope ts(kTimeTrsm, s);
@@ -463,8 +491,7 @@ int run_pipeline_sym(Operator &op, const rpca_opts *o, bool nystrom, float *U, i
     RPCA_TRY(renorm_n(c, true));
     {
         TimedScope ts(kTimeSmallSvd, s);
-        RPCA_TRY(launch_small_svd(racc0, l, lp, L.k, L.kp, wk, zk, sig, c.at<float>(L.rot), c.at<float>(L.zbuf),
-                                  c.at<int>(L.perm), c.st, s));
+        RPCA_TRY(small_svd_step(c, wk, zk, sig));
     }
     TimedScope ts_lift(kTimeLift, s);
     RPCA_TRY(launch_sgemm(false, n, L.k, lp, x1, lp, zk, L.kp, U, ldu, 1, 0, s));

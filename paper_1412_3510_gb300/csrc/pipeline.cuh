@@ -33,8 +33,8 @@ struct Layout {
     int s_adj = 0, s_gram_m = 0, s_gram_n = 0, cchunks = 0;
     size_t status = 0, x0 = 0, x1 = 0, y0 = 0, y1 = 0, part = 0, cpart = 0, qpart = 0, G = 0,
            rinv = 0, racc0 = 0, racc1 = 0, wk = 0, zk = 0, sig = 0, perm = 0, rot = 0, zbuf = 0,
-           rinv_m = 0, flags = 0, scal = 0, cvec = 0, bias = 0, lu0 = 0, lu1 = 0, rsplit = 0, scratch = 0,
-           total = 0;
+           rinv_m = 0, flags = 0, scal = 0, cvec = 0, bias = 0, bpart = 0, r32 = 0, wfull = 0, zfull = 0, svd64 = 0, lu0 = 0,
+           lu1 = 0, rsplit = 0, scratch = 0, total = 0;
 };
 
 Layout make_layout(int64_t m, int64_t n, int l, int k, int adjoint_splits, size_t op_scratch);

@@ -186,34 +186,45 @@ adjoint_reduce_kernel(const float *__restrict__ part, int splits, int64_t rows, 
     }
 }
 
-// bias[j] = sum_i c[i] X[i][j] (j < l), 0 for l <= j < lp.  A CTA owns 32 columns
-// (threadIdx.x) with eight interleaved row groups (threadIdx.y), each a compensated
-// sum; the eight group sums are combined in order (deterministic).
+// bias[j] = sum_i c[i] X[i][j] (j < l), 0 for l <= j < lp, in two deterministic stages:
+// CTA b sums the rows [b rows_per, (b + 1) rows_per) into part[b][j] (a warp reads 32
+// consecutive columns of a row, eight warps take interleaved rows, the eight sums are
+// combined in order), then one CTA adds the partials in CTA order (compensated).
+constexpr int kCentreRowsPer = 64;
 __global__ void __launch_bounds__(256)
-centring_row_kernel(const float *__restrict__ c, const float *__restrict__ X, int64_t n, int l, int lp,
-                    float *__restrict__ bias) {
-    __shared__ float sh[8][32], ch[8][32];
-    const int j = blockIdx.x * 32 + threadIdx.x, y = threadIdx.y;
-    float s = 0.f, comp = 0.f;
-    if (j < l)
-        for (int64_t i = y; i < n; i += 8) {
-            const float v = c[i] * X[i * lp + j] - comp;
-            const float t = s + v;
-            comp = (t - s) - v;
-            s = t;
+centring_part_kernel(const float *__restrict__ c, const float *__restrict__ X, int64_t n, int l, int lp,
+                     float *__restrict__ part) {
+    __shared__ float sh[8][32];
+    const int64_t r0 = (int64_t)blockIdx.x * kCentreRowsPer, r1 = min(n, r0 + kCentreRowsPer);
+    const int y = threadIdx.y;
+    for (int cb = 0; cb < lp; cb += 32) {
+        const int j = cb + threadIdx.x;
+        float acc = 0.f;
+        if (j < l)
+            for (int64_t i = r0 + y; i < r1; i += 8) acc = fmaf(c[i], X[i * lp + j], acc);
+        sh[y][threadIdx.x] = acc;
+        __syncthreads();
+        if (y == 0 && j < lp) {
+            float t = 0.f;
+            for (int g = 0; g < 8; ++g) t += sh[g][threadIdx.x];
+            part[(int64_t)blockIdx.x * lp + j] = t;
         }
-    sh[y][threadIdx.x] = s;
-    ch[y][threadIdx.x] = comp;
-    __syncthreads();
-    if (y == 0 && j < lp) {
-        float t = 0.f, cc = 0.f;
-        for (int g = 0; g < 8; ++g) {
-            const float v = (sh[g][threadIdx.x] - ch[g][threadIdx.x]) - cc;
-            const float u = t + v;
-            cc = (u - t) - v;
-            t = u;
-        }
-        bias[j] = j < l ? t : 0.f;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+centring_sum_kernel(const float *__restrict__ part, int nparts, int l, int lp, float *__restrict__ bias) {
+    for (int j = threadIdx.x; j < lp; j += blockDim.x) {
+        float s = 0.f, comp = 0.f;
+        if (j < l)
+            for (int b = 0; b < nparts; ++b) {
+                const float v = part[(int64_t)b * lp + j] - comp;
+                const float t = s + v;
+                comp = (t - s) - v;
+                s = t;
+            }
+        bias[j] = s;
     }
 }
 
@@ -272,8 +283,14 @@ int launch_adjoint_reduce(const float *part, int splits, int64_t rows, int l, in
     return RPCA_OK;
 }
 
-int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *bias, cudaStream_t s) {
-    centring_row_kernel<<<(unsigned)cdiv(lp, 32), dim3(32, 8), 0, s>>>(c, X, n, l, lp, bias);
+int centring_parts(int64_t n) { return (int)cdiv(std::max<int64_t>(n, 1), kCentreRowsPer); }
+
+int launch_centring_row(const float *c, const float *X, int64_t n, int l, int lp, float *part, float *bias,
+                        cudaStream_t s) {
+    const int nb = centring_parts(n);
+    centring_part_kernel<<<(unsigned)nb, dim3(32, 8), 0, s>>>(c, X, n, l, lp, part);
+    RPCA_CHECK_LAUNCH();
+    centring_sum_kernel<<<1, 256, 0, s>>>(part, nb, l, lp, bias);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

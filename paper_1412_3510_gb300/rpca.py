@@ -51,14 +51,14 @@ def _rowmajor_ld(t: torch.Tensor, name: str) -> int:
 
 
 def make_opts(k, l=None, its=2, raw=False, seed=0, precision="fp32", renorm="cholqr",
-              omega=None, col_weights=None, odd_only=False) -> L.RpcaOpts:
+              omega=None, col_weights=None, odd_only=False, small_fp64=False) -> L.RpcaOpts:
     o = L.RpcaOpts()
     o.k = int(k)
     o.l = int(k + 2 if l is None else l)
     o.its = int(its)
     o.raw = int(bool(raw))
     o.seed = int(seed) & ((1 << 64) - 1)
-    o.precision = L.PREC[precision]
+    o.precision = L.PREC[precision] | (L.RPCA_PREC_SMALL_FP64 if small_fp64 else 0)
     o.renorm = L.RENORM[renorm] | (L.RPCA_RENORM_ODD_ONLY if odd_only else 0)
     o.omega = None if omega is None else omega.data_ptr()
     o.col_weights = None if col_weights is None else col_weights.data_ptr()
@@ -78,7 +78,7 @@ def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw:
                seed: int = 0, precision: str = "fp32", renorm: str = "cholqr",
                omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
                ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
-               odd_only: bool = False):
+               odd_only: bool = False, small_fp64: bool = False):
     """Randomized PCA A_c ~ U diag(S) V^T (Sections 2 and 5 of the paper).
 
     A: m x n float32 CUDA tensor, row-major (any leading dimension >= n).
@@ -94,7 +94,7 @@ def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw:
     if col_weights is not None:
         _need_cuda(col_weights, "col_weights")
         col_weights = col_weights.contiguous()
-    opts = make_opts(k, l, its, raw, seed, precision, renorm, omega, col_weights, odd_only)
+    opts = make_opts(k, l, its, raw, seed, precision, renorm, omega, col_weights, odd_only, small_fp64)
     lib = L.load()
     need = rpca_dense_workspace_size(m, n, opts)
     if need == 0:
@@ -119,7 +119,8 @@ def rpca_dense(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, raw:
     return U, S, V
 
 
-def _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, nystrom):
+def _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, nystrom,
+              small_fp64=False):
     _need_cuda(A, "A")
     lda = _rowmajor_ld(A, "A")
     n = A.shape[0]
@@ -128,7 +129,7 @@ def _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, s
     if omega is not None:
         _need_cuda(omega, "omega")
         omega = omega.contiguous()
-    opts = make_opts(k, l, its, True, seed, precision, renorm, omega, None, odd_only)
+    opts = make_opts(k, l, its, True, seed, precision, renorm, omega, None, odd_only, small_fp64)
     lib = L.load()
     need = int(lib.rpca_sym_workspace_size(n, C.byref(opts)))
     if need == 0:
@@ -156,19 +157,43 @@ def _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, s
 
 def rpca_sym(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, seed: int = 0,
              precision: str = "fp32", renorm: str = "cholqr", omega: torch.Tensor | None = None,
-             odd_only: bool = False, ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True):
+             odd_only: bool = False, ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
+             small_fp64: bool = False):
     """Self-adjoint A (n x n): Section 5's loop of products with A only, then
     B = Q^T A Q; returns (U, S, V) with A ~ U diag(S) V^T, V = U diag(sign(lambda))."""
-    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, False)
+    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, False, small_fp64)
 
 
 def rpca_nystrom(A: torch.Tensor, k: int, l: int | None = None, its: int = 2, seed: int = 0,
                  precision: str = "fp32", renorm: str = "cholqr", omega: torch.Tensor | None = None,
                  odd_only: bool = False, ws: torch.Tensor | None = None, out=None, stream=None,
-                 check: bool = True):
+                 check: bool = True, small_fp64: bool = False):
     """Stabilised Nystrom approximation of a nonnegative-definite A (Section 3):
     returns (U, S) with A ~ U diag(S) U^T."""
-    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, True)
+    return _sym_call(A, k, l, its, seed, precision, renorm, omega, odd_only, ws, out, stream, check, True, small_fp64)
+
+
+def rpca_small_svd(M: torch.Tensor, stream=None):
+    """SVD of a small FP64 matrix M (l x l, CUDA) as the FP64 l x l path computes it:
+    returns (S, W, Z) with M = W diag(S) Z^T."""
+    if not isinstance(M, torch.Tensor) or not M.is_cuda or M.dtype != torch.float64:
+        raise ValueError("M must be a float64 CUDA tensor")
+    l = int(M.shape[0])
+    if M.dim() != 2 or M.shape[1] != l:
+        raise ValueError("M must be square")
+    M = M.contiguous()
+    lib = L.load()
+    need = int(lib.rpca_small_svd_workspace_size(l))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_small_svd_workspace_size")
+    ws = workspace(need, M.device)
+    S = torch.empty(l, dtype=torch.float64, device=M.device)
+    W = torch.empty(l, l, dtype=torch.float64, device=M.device)
+    Z = torch.empty(l, l, dtype=torch.float64, device=M.device)
+    _check(lib.rpca_small_svd(_ptr(M), l, _ptr(S), _ptr(W), _ptr(Z), _ptr(ws), ws.numel(), _stream(stream)),
+           "rpca_small_svd")
+    _check(rpca_read_status(ws, stream), "rpca_small_svd (device)")
+    return S, W, Z
 
 
 def rpca_read_status(ws: torch.Tensor, stream=None) -> int:
@@ -293,7 +318,7 @@ def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, sh
              l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
              omega: torch.Tensor | None = None, col_weights: torch.Tensor | None = None,
              ws: torch.Tensor | None = None, out=None, stream=None, check: bool = True,
-             renorm: str = "cholqr", odd_only: bool = False):
+             renorm: str = "cholqr", odd_only: bool = False, small_fp64: bool = False):
     """Randomized PCA of a CSR matrix (row_ptr int32 m+1, col_idx int32 nnz, val float32 nnz)."""
     m, n = int(shape[0]), int(shape[1])
     _need_i32(row_ptr, "row_ptr")
@@ -306,7 +331,7 @@ def rpca_csr(row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, sh
     if col_weights is not None:
         _need_cuda(col_weights, "col_weights")
         col_weights = col_weights.contiguous()
-    opts = make_opts(k, l, its, raw, seed, "fp32", renorm, omega, col_weights, odd_only)
+    opts = make_opts(k, l, its, raw, seed, "fp32", renorm, omega, col_weights, odd_only, small_fp64)
     lib = L.load()
     need = int(lib.rpca_csr_workspace_size(m, n, nnz, C.byref(opts)))
     if need == 0:
