@@ -700,6 +700,49 @@ def learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream):
             "fallback": "dense entry point only (rpca_dense_learned); the batched form reports accuracy"}
 
 
+def error_vs_fp64(A, k, l, its, raw, seed, iters, ws, U, S, V):
+    """Each precision form's outputs against the FP64 oracle's on the same FP32 A and the
+    GPU's own Omega: largest relative sigma error (all k, and the leading half), the
+    sine of the largest principal angle between the U subspaces (leading k, and the
+    leading half), and the relative difference of the Section 4 residual estimates
+    (GPU estimator on both factor sets, `iters` iterations, same start)."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1412_3510_gb300 as rp
+    m, n = A.shape
+    Ah = A.cpu().numpy()
+    om = rp.rpca_gaussian_omega(n, l, seed).double().cpu().numpy()
+    t0 = time.perf_counter()
+    Uo, so, Vo = oracle.rpca(Ah, k, l, its, raw=raw, seed=seed, omega=om)
+    t_or = time.perf_counter() - t0
+    del Ah
+    dev = A.device
+    f32 = [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev) for x in (Uo, so, Vo)]
+    est_o = rp.rpca_resid_norm(A, *f32, raw=raw, iters=iters, seed=7)
+    half = max(1, k // 2)
+
+    def angle(X, Y):
+        Qx, _ = np.linalg.qr(X)
+        Qy, _ = np.linalg.qr(Y)
+        c = np.linalg.svd(Qx.T @ Qy, compute_uv=False).min()
+        return float(np.sqrt(max(0.0, 1.0 - c * c)))
+    forms = {}
+    for name, prec, small in (("fp32", "fp32", False), ("bf16x3", "bf16x3", False),
+                              ("fp32+fp64_lxl", "fp32", True), ("bf16x3+fp64_lxl", "bf16x3", True)):
+        rp.rpca_dense(A, k, l, its=its, raw=raw, seed=seed, precision=prec, small_fp64=small, ws=ws, out=(U, S, V))
+        est = rp.rpca_resid_norm(A, U, S, V, raw=raw, iters=iters, seed=7)
+        sg = S.double().cpu().numpy()
+        Ug = U.double().cpu().numpy()
+        rel = np.abs(sg - so) / so
+        forms[name] = {"sigma_max_rel": float(rel.max()), "sigma_max_rel_leading_half": float(rel[:half].max()),
+                       "u_subspace_sin_k": angle(Ug, Uo), "u_subspace_sin_leading_half": angle(Ug[:, :half],
+                                                                                                 Uo[:, :half]),
+                       "resid_rel": float(abs(est - est_o) / est_o)}
+    return {"oracle": f"FP64 numpy oracle on the same FP32 A with the GPU's Omega, its={its} ({t_or:.1f} s)",
+            "resid_estimator": f"{iters} iterations, same start vector, on each factor set", "forms": forms}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -720,6 +763,9 @@ def main():
     ap.add_argument("--resid-iters", type=int, default=20)
     ap.add_argument("--resid-iters-conv", type=int, default=60,
                     help="estimator iterations for the accuracy verdict (converged on the workloads here)")
+    ap.add_argument("--error-vs-fp64", default="auto", choices=["auto", "on", "off"],
+                    help="record every precision form's error against the FP64 oracle on the same A (auto: "
+                         "dense workloads up to 4e8 entries)")
     ap.add_argument("--configured-its", action="store_true",
                     help="time the configured its even when it misses resid <= 1.1 sigma_{k+1}")
     ap.add_argument("--ref-rows", type=int, default=50000)
@@ -1004,10 +1050,10 @@ def main():
     if not args.no_forms and not csr:
         side_steps = max(10, min(args.steps, 50))
 
-        def time_form(precision, its_f, renorm="cholqr"):
+        def time_form(precision, its_f, renorm="cholqr", small_fp64=False):
             def once():
                 rp.rpca_dense(A, k, l, its=its_f, raw=raw, seed=1 + rank, precision=precision, ws=ws,
-                              out=(U, S, V), check=False, renorm=renorm)
+                              out=(U, S, V), check=False, renorm=renorm, small_fp64=small_fp64)
             for _ in range(args.warmup):
                 once()
             g_form = capture_graph(rp, once)[0] if graph is not None else None
@@ -1039,6 +1085,12 @@ def main():
         forms["plain_fp32"] = {"its": its, "value": world / (ms_fp32 / 1e3), "ms_per_step": ms_fp32,
                                "steps": side_steps, "resid_over_sigma_k1": est_fp32 / sk1,
                                "speedup_of_headline": ms_fp32 / ms_per_step}
+        # the l x l work in FP64 (Cholesky, inverse, accumulated factor, SVD of R^T)
+        ms_64 = time_form(args.precision, its, small_fp64=True)
+        est_64 = estimate(args.resid_iters_conv)
+        forms["small_fp64"] = {"its": its, "value": world / (ms_64 / 1e3), "ms_per_step": ms_64, "steps": side_steps,
+                               "precision": args.precision + "+fp64 l x l", "resid_over_sigma_k1": est_64 / sk1,
+                               "time_vs_headline": ms_64 / ms_per_step}
         if w.get("its_sweep"):
             # Section 7's study of the number of power iterations on this workload
             sweep = {}
@@ -1054,6 +1106,13 @@ def main():
             forms["lu_renorm"] = {"its": its, "value": world / (ms_lu / 1e3), "ms_per_step": ms_lu,
                                   "steps": side_steps, "precision": args.precision,
                                   "resid_over_sigma_k1": est_lu / sk1, "speedup_of_headline": ms_lu / ms_per_step}
+
+    # error of every precision form against the FP64 oracle run on the very same matrix and
+    # Omega (sigma, U subspace, residual), at the headline's its
+    err64 = None
+    want_err = args.error_vs_fp64 == "on" or (args.error_vs_fp64 == "auto" and not csr and m * n <= 4e8)
+    if want_err and not csr and rank == 0:
+        err64 = error_vs_fp64(A, k, l, its, raw, 1 + rank, args.resid_iters_conv, ws, U, S, V)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1124,6 +1183,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "forms": forms,
+        "error_vs_fp64": err64,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -459,7 +459,9 @@ __device__ void small_svd(Smem &sm, int l) {
                 if (q < l && fabsf(ga) > tol * sqrtf(al * be) && ga != 0.f) {
                     const float zeta = (be - al) / (2.f * ga);
                     const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(zeta, 1.f));
-                    const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+                    // correctly rounded: an approximate rsqrt would shrink the column norms
+                    // (the singular values) a little with every rotation
+                    const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = cs * t;
                     if (lane < l) {
                         M[p * l + lane] = cs * x - sn * y;
                         M[q * l + lane] = sn * x + cs * y;

@@ -287,7 +287,9 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
                     const float t = __shfl_sync(0xffffffffu, thr, j);
                     const bool good = j >= bl || (d > t && d > 0.f);
                     fail |= !good;                          // uniform: every lane sees d
-                    a[j] *= rsqrtf(j < bl && good ? d : 1.f);   // row j of R: r_jc (lane j: sqrt(d))
+                    // row j of R: r_jc (lane j: sqrt(d)); correctly rounded, as the factor's scale
+                    // reaches the singular values through the accumulated R
+                    a[j] /= sqrtf(j < bl && good ? d : 1.f);
                     if (lane == j) rd = a[j];
                     // constant trip counts (r > j resolved at compile time) keep a[] in registers
 #pragma unroll

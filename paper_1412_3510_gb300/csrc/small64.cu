@@ -16,7 +16,7 @@
 //    accuracy; steps of the iterative refinement of Ogita & Aishima
 //    ("Iterative refinement for singular value decomposition based on matrix
 //    multiplication", J. Comput. Appl. Math. 369, 2020) take them to FP64
-//    accuracy (three steps).  A step is six l x l products in FP64 (spread over all SMs) plus
+//    accuracy (five steps).  A step is six l x l products in FP64 (spread over all SMs) plus
 //    O(l^2) elementwise work:
 //      Rm = I - W^T W, Sm = I - Z^T Z, T = W^T (M Z)      (M = R^T)
 //      sigma_i = T_ii / (1 - (Rm_ii + Sm_ii) / 2)
@@ -37,8 +37,9 @@ namespace {
 
 constexpr int kCholThreads = 1024;
 // refinement steps: each squares the relative error divided by the relative gap of the
-// closest pair (from FP32's 1e-7: 1e-14 / gap, then 1e-28 / gap^3)
-constexpr int kRefineSteps = 3;
+// closest pair; the FP32 Jacobi leaves the left vectors of the smallest values with
+// errors up to u sigma_1 / sigma_i, which five steps bring to FP64 level
+constexpr int kRefineSteps = 5;
 
 __device__ __forceinline__ int packed_row(int i, int l) { return i * l - (i * (i - 1)) / 2; }
 

@@ -22,7 +22,6 @@ namespace {
 
 constexpr int kJacThreads = 1024;
 constexpr int kMaxSweeps = 40;
-constexpr float kQuadStop = 5e-4f;    // see the end of a sweep in jacobi_kernel
 
 __host__ __device__ __forceinline__ int even_up(int l) { return l + (l & 1); }
 // row length of the Jacobi CTA's copy of M (16-byte rows for float4 access)
@@ -41,7 +40,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
     const int ldm = jac_ldm(l);        // multiple of 4, columns l..ldm-1 zero
     const int nv = ldm / 4;            // float4 per row
     __shared__ int s_rot;
-    __shared__ int s_mu;               // largest |c| / sqrt(a b) of the sweep (float bits, >= 0)
+    __shared__ int s_mu;               // largest predicted next-sweep measure (float bits, >= 0)
     __shared__ float s_sig[RPCA_MAX_L];
     const int tid = threadIdx.x;
     const int L = even_up(l);
@@ -104,16 +103,22 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                 b += __shfl_xor_sync(0xffffffffu, b, off);
                 c += __shfl_xor_sync(0xffffffffu, c, off);
             }
-            // the rotation that zeroes c (Rutishauser's formulas); only its
-            // orthogonality matters, so the angle is computed with fast intrinsics:
-            // cs^2 + sn^2 = 1 to rounding whatever the error in t
+            // the rotation that zeroes c (Rutishauser's formulas).  Only its orthogonality
+            // matters: the angle t may carry fast-intrinsic error, but cs = 1 / sqrt(1 + t^2)
+            // is formed with the correctly rounded square root and division, so that
+            // cs^2 + sn^2 = 1 to unbiased rounding -- an approximate reciprocal square root
+            // shrinks both columns by ~1e-8 per rotation, a systematic drift of the column
+            // norms (the singular values) over the hundreds of rotations a column takes
             float cs = 1.f, sn = 0.f;
             const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
             if (mu > tol) {
-                mu_max = fmaxf(mu_max, mu);
+                // by quadratic convergence the next sweep's measure for this pair is about
+                // mu^2 / delta, delta the relative gap of the two squared column norms
+                const float delta = fabsf(b - a) / (a + b);
+                mu_max = fmaxf(mu_max, delta > 0.f ? fminf(mu * mu / delta, 1.f) : 1.f);
                 const float zeta = __fdividef(b - a, 2.f * c);
                 const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-                cs = rsqrtf(fmaf(t, t, 1.f));
+                cs = 1.f / sqrtf(fmaf(t, t, 1.f));
                 sn = cs * t;
                 if (CACHE > 0) {
 #pragma unroll
@@ -151,9 +156,10 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
         if ((tid & 31) == 0 && mu_max > 0.f) atomicMax(&s_mu, __float_as_int(mu_max));
         __syncthreads();
         if (s_rot == 0) { ++sweep; break; }
-        // quadratic convergence: after a sweep whose rotations all had measure below
-        // kQuadStop the next sweep's measures are below tol, so it is not run
-        if (__int_as_float(s_mu) < kQuadStop) { ++sweep; early = true; break; }
+        // quadratic convergence: when every rotation's predicted next measure is below
+        // tol the next sweep would rotate nothing, so it is not run (pairs of nearly
+        // equal column norms, small delta, keep the iteration going longer)
+        if (__int_as_float(s_mu) < tol) { ++sweep; early = true; break; }
         __syncthreads();
     }
     // sweep = number of logged sweeps (the last one made no rotation or only rotations
@@ -194,206 +200,6 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
             const int j = perm[r];
             const float s = s_sig[j];
             v = s > 0.f ? Ms[j * ldm + i] / s : 0.f;
-        }
-        Wk[e] = v;
-    }
-}
-
-// The same one-sided Jacobi with the column pairs held in registers (l <= 128).
-// Group g (8 lanes) owns pair g of every round; lane t of a group holds elements
-// t, t + 8, ... of its two columns (x: the slot at circle position g, y: the slot at
-// position L-1-g).  After the rotation the columns move one position along the
-// circle, data at position p taking the place of position p - 1 (position 0 fixed):
-// tops move down one group (shfl_down by 8 lanes), bottoms up one group (shfl_up),
-// group P-1's bottom becomes its top and group 1's top becomes group 0's bottom.  So
-// group g handles at step s exactly the columns f^s(g), f^s(L-1-g) that
-// jacobi_kernel assigns it (f(0) = 0, f(L-1) = 1, f(p) = p + 1), the rotation log has
-// the same layout, and replay_kernel serves both.  Only the columns that cross a warp
-// boundary go through shared memory (double buffered by round parity, one barrier a
-// round).  A sweep ends the iteration early when every rotation's measure mu would,
-// by quadratic convergence, fall below tol in the next sweep: mu^2 / delta < tol with
-// delta = |b - a| / (a + b) the relative gap of the pair's squared norms (clustered
-// values, small delta, take more sweeps).
-template <int E>
-__global__ void __launch_bounds__(512)
-jacobi_reg_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int *__restrict__ sweeps_out,
-                  float *__restrict__ sig, int *__restrict__ perm, float *__restrict__ Wk, int lp, int k, int kp,
-                  DevStatus *__restrict__ st) {
-    constexpr int G = 8;
-    constexpr int kWarps = 16;
-    __shared__ float xdown[2][kWarps][G][E];      // tops leaving a warp's first group for the previous warp
-    __shared__ float yup[2][kWarps][G][E];        // bottoms leaving a warp's last group for the next warp
-    __shared__ float s_sig[RPCA_MAX_L];
-    extern __shared__ float Ms[];                 // final columns (row id, stride 129), for the outputs
-    __shared__ int s_rot;
-    __shared__ int s_pred;                        // largest predicted next-sweep measure (float bits)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = tid / G, t = tid % G;
-    const int L = l + (l & 1), P = L / 2;
-    const bool live = g < P;
-    const float tol = 8.0f * sqrtf((float)l) * 0x1p-24f;
-
-    // initial columns: slot x = column g, slot y = column L-1-g (column l, when l is odd, is zero)
-    int idx = live ? g : 0, idy = live ? L - 1 - g : 0;
-    float x[E], y[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-        const int e = t + G * i;
-        x[i] = (live && idx < l && e < l) ? R[(size_t)idx * l + e] : 0.f;
-        y[i] = (live && idy < l && e < l) ? R[(size_t)idy * l + e] : 0.f;
-    }
-    float2 *rlog = rot + g;
-    int sweep = 0;
-    bool early = false;
-    int round = 0;
-    for (; sweep < kMaxSweeps; ++sweep) {
-        if (tid == 0) { s_rot = 0; s_pred = 0; }
-        __syncthreads();
-        float pred_max = 0.f;
-        for (int step = 0; step < L - 1; ++step, ++round) {
-            float a0 = 0.f, b0 = 0.f, c0 = 0.f, a1 = 0.f, b1 = 0.f, c1 = 0.f;
-#pragma unroll
-            for (int i = 0; i < E; i += 2) {
-                a0 = fmaf(x[i], x[i], a0);
-                b0 = fmaf(y[i], y[i], b0);
-                c0 = fmaf(x[i], y[i], c0);
-                if (i + 1 < E) {
-                    a1 = fmaf(x[i + 1], x[i + 1], a1);
-                    b1 = fmaf(y[i + 1], y[i + 1], b1);
-                    c1 = fmaf(x[i + 1], y[i + 1], c1);
-                }
-            }
-            float a = a0 + a1, b = b0 + b1, c = c0 + c1;
-#pragma unroll
-            for (int off = 1; off < G; off <<= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, off);
-                b += __shfl_xor_sync(0xffffffffu, b, off);
-                c += __shfl_xor_sync(0xffffffffu, c, off);
-            }
-            // the rotation zeroing x . y, computed in the slots' own order; the log keeps
-            // the orientation (lower column index first) the replay uses: swapping the
-            // roles of the two columns flips the sign of sn and leaves the rotation of the
-            // data unchanged
-            float cs = 1.f, sn = 0.f;
-            const bool valid = live && idx < l && idy < l;
-            const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
-            if (mu > tol) {
-                const float delta = fabsf(b - a) / (a + b);
-                pred_max = fmaxf(pred_max, delta > 0.f ? fminf(mu * mu / delta, 1.f) : 1.f);
-                const float zeta = __fdividef(b - a, 2.f * c);
-                const float tt = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-                cs = rsqrtf(fmaf(tt, tt, 1.f));
-                sn = cs * tt;
-#pragma unroll
-                for (int i = 0; i < E; ++i) {
-                    const float xi = x[i], yi = y[i];
-                    x[i] = cs * xi - sn * yi;
-                    y[i] = sn * xi + cs * yi;
-                }
-                s_rot = 1;
-            }
-            if (live && t == 0) *rlog = make_float2(cs, idx < idy ? sn : -sn);
-            rlog += P;
-            // move one position along the circle
-            const int par = round & 1;
-            const int gw = g & 3;                          // group within the warp
-            if (live && gw == 0 && g >= 4) {
-#pragma unroll
-                for (int i = 0; i < E; ++i) xdown[par][warp][t][i] = x[i];
-            }
-            if (live && gw == 3 && g + 1 < P) {
-#pragma unroll
-                for (int i = 0; i < E; ++i) yup[par][warp][t][i] = y[i];
-            }
-            float xn[E], yn[E];
-#pragma unroll
-            for (int i = 0; i < E; ++i) {
-                xn[i] = __shfl_down_sync(0xffffffffu, x[i], G);
-                yn[i] = __shfl_up_sync(0xffffffffu, y[i], G);
-            }
-            __syncthreads();
-            if (live && P > 1) {                           // (one pair: nothing moves)
-                if (g == 0) {                              // top fixed; bottom from group 1's top
-#pragma unroll
-                    for (int i = 0; i < E; ++i) yn[i] = xn[i], xn[i] = x[i];
-                } else {
-                    // top: from group g + 1 (group P-1: its own bottom)
-                    if (g == P - 1) {
-#pragma unroll
-                        for (int i = 0; i < E; ++i) xn[i] = y[i];
-                    } else if (gw == 3) {
-#pragma unroll
-                        for (int i = 0; i < E; ++i) xn[i] = xdown[par][warp + 1][t][i];
-                    }
-                    // bottom: from group g - 1
-                    if (gw == 0) {
-#pragma unroll
-                        for (int i = 0; i < E; ++i) yn[i] = yup[par][warp - 1][t][i];
-                    }
-                }
-                // the column ids follow the schedule f (they need not travel with the data)
-                idx = idx == 0 ? 0 : (idx == L - 1 ? 1 : idx + 1);
-                idy = idy == 0 ? 0 : (idy == L - 1 ? 1 : idy + 1);
-#pragma unroll
-                for (int i = 0; i < E; ++i) { x[i] = xn[i]; y[i] = yn[i]; }
-            }
-        }
-        // the sweep's largest predicted next measure (warp max, one atomic per warp)
-#pragma unroll
-        for (int off = 16; off; off >>= 1) pred_max = fmaxf(pred_max, __shfl_xor_sync(0xffffffffu, pred_max, off));
-        if (lane == 0 && pred_max > 0.f) atomicMax(&s_pred, __float_as_int(pred_max));
-        __syncthreads();
-        if (s_rot == 0) { ++sweep; break; }
-        if (__int_as_float(s_pred) < tol) { ++sweep; early = true; break; }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        *sweeps_out = sweep;
-        st->jacobi_sweeps = sweep;
-        if (sweep >= kMaxSweeps && s_rot != 0 && !early) atomicAdd(&st->jacobi_unconverged, 1);
-    }
-    // column norms = singular values; the columns back to shared memory by id
-    float nx2 = 0.f, ny2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < E; ++i) { nx2 = fmaf(x[i], x[i], nx2); ny2 = fmaf(y[i], y[i], ny2); }
-#pragma unroll
-    for (int off = 1; off < G; off <<= 1) {
-        nx2 += __shfl_xor_sync(0xffffffffu, nx2, off);
-        ny2 += __shfl_xor_sync(0xffffffffu, ny2, off);
-    }
-    if (live) {
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const int e = t + G * i;
-            if (e < l) {
-                if (idx < l) Ms[idx * 129 + e] = x[i];
-                if (idy < l) Ms[idy * 129 + e] = y[i];
-            }
-        }
-        if (t == 0) {
-            if (idx < l) s_sig[idx] = sqrtf(nx2);
-            if (idy < l) s_sig[idy] = sqrtf(ny2);
-        }
-    }
-    __syncthreads();
-    for (int j = tid; j < l; j += blockDim.x) {
-        const float sj = s_sig[j];
-        int rank = 0;
-        for (int i = 0; i < l; ++i) {
-            const float si = s_sig[i];
-            rank += (si > sj) || (si == sj && i < j);
-        }
-        perm[rank] = j;
-        sig[rank] = sj;
-    }
-    __syncthreads();
-    for (int e = tid; e < lp * kp; e += blockDim.x) {
-        const int i = e / kp, r = e % kp;
-        float v = 0.f;
-        if (i < l && r < k) {
-            const int j = perm[r];
-            const float sv = s_sig[j];
-            v = sv > 0.f ? Ms[j * 129 + i] / sv : 0.f;
         }
         Wk[e] = v;
     }
@@ -538,26 +344,18 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
     const int smem_max = (int)((size_t)RPCA_MAX_L * jac_ldm(RPCA_MAX_L) * sizeof(float));
     // l <= 128 (at most 32 float4 per column): four lanes per pair with eight float4
     // of each column in registers; wider: eight lanes per pair, columns re-read
-    if (l <= 128) {
-        // columns in registers, eight lanes per pair
-        const int threads = (int)std::max<int64_t>(64, round_up(8 * (even_up(l) / 2), 32));
-        float2 *rl = reinterpret_cast<float2 *>(rot);
-        const size_t dsm = (size_t)l * 129 * sizeof(float);
-        auto kern = l <= 32 ? jacobi_reg_kernel<4> : l <= 64 ? jacobi_reg_kernel<8> : jacobi_reg_kernel<16>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 129 * (int)sizeof(float)) !=
-            cudaSuccess)
-            return RPCA_ERR_CUDA;
-        kern<<<1, threads, dsm, s>>>(R, l, rl, sweeps, sig, perm, Wk, lp, k, kp, st);
-        RPCA_CHECK_LAUNCH();
-    } else {
-        auto kern = jacobi_kernel<8, 0>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
-            return RPCA_ERR_CUDA;
-        // eight lanes per column pair of a round; no idle warps at the round barriers
-        const int threads = (int)std::min<int64_t>(kJacThreads, std::max<int64_t>(64, round_up(8 * (even_up(l) / 2), 32)));
-        kern<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig, perm, Wk, lp, k, kp, st);
-        RPCA_CHECK_LAUNCH();
-    }
+    // l <= 128 (at most 32 float4 per column): four lanes per pair with eight float4
+    // of each column in registers; wider: eight lanes per pair, columns re-read
+    const bool cached = jac_ldm(l) / 4 <= 4 * 8;
+    auto kern = cached ? jacobi_kernel<4, 8> : jacobi_kernel<8, 0>;
+    const int lpp = cached ? 4 : 8;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) != cudaSuccess)
+        return RPCA_ERR_CUDA;
+    // lpp lanes per column pair of a round; no idle warps at the round barriers
+    const int threads = (int)std::min<int64_t>(cached ? 512 : kJacThreads,
+                                               std::max<int64_t>(64, round_up(lpp * (even_up(l) / 2), 32)));
+    kern<<<1, threads, smem, s>>>(R, l, reinterpret_cast<float2 *>(rot), sweeps, sig, perm, Wk, lp, k, kp, st);
+    RPCA_CHECK_LAUNCH();
     const int grid = (int)cdiv(lp, kReplayWarps);
     const size_t rsmem = (size_t)2 * kReplayChunk * (even_up(l) / 2) * sizeof(float2);
     if (cudaFuncSetAttribute(replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
