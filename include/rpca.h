@@ -224,6 +224,28 @@ int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int64_t max_m, 
                       float *ms);
 
 /* ------------------------------------------------------------------------
+ * The batched form with learned test-matrix weights and the fallback of
+ * rpca_dense_learned, for every matrix of the batch:
+ *   rpca_batched with col_weights (the learned diag(d) Omega per matrix);
+ *   the Section 4 estimate of ||A_c - U diag(S) V^T|| (resid_iters power
+ *   iterations from the start vector of rpca_resid_norm, stream (o->seed, 1));
+ *   matrices whose estimate exceeds fallback_ratio * s_{k+1} (s_{k+1} of the same
+ *   run's rank-l approximation; only when l > k) are computed again with the
+ *   plain Gaussian Omega, in one more launch that skips the others.
+ * item_status (NULL or count int32, device): 0 = kept the learned result,
+ * RPCA_FELL_BACK = recomputed with the plain sketch, < 0 = error as rpca_batched.
+ * est_out (NULL or 2 * count floats, device): per matrix the learned run's
+ * estimate and s_{k+1}.  Other arguments as rpca_batched.  The status word in
+ * ws reports the last launch (per-matrix errors are in item_status).  No host
+ * synchronisation.  ws: rpca_batched_learned_workspace_size(...) bytes.
+ * ---------------------------------------------------------------------- */
+size_t rpca_batched_learned_workspace_size(int32_t count, int64_t max_m, int64_t max_n, const rpca_opts *o);
+int rpca_batched_learned(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n,
+                         const rpca_opts *o, const float *const *col_weights, int32_t resid_iters,
+                         float fallback_ratio, int32_t *item_status, float *est_out, void *ws, size_t ws_bytes,
+                         rpca_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Spectral-norm residual estimate ||A_c - U diag(S) V^T||_2 by the power
  * method from a random start (Section 4).
  *
@@ -407,6 +429,17 @@ int rpca_small_svd(const double *M, int32_t l, double *S, double *W, double *Z, 
  * key (key0, key1)) for b < nblocks (device output). */
 int rpca_philox4x64_10(uint64_t key0, uint64_t key1, uint64_t first, int64_t nblocks,
                        uint64_t *out, rpca_stream_t stream);
+
+/* Check of the bounded device-side waits: one CTA waits, with the wait the
+ * pipelined kernels use (an mbarrier try-wait loop bounded in clock cycles), on an
+ * mbarrier that nothing ever arrives on; after limit_cycles (1000 .. 2e9) it gives
+ * up and records RPCA_ERR_TIMEOUT in the status block at the start of ws
+ * (>= 512 bytes, 256-byte aligned), as a pipelined kernel does when an arrival is
+ * lost.  *waited_cycles (host) receives the cycles the wait took.  Waits for
+ * `stream`.  rpca_read_status(ws, ...) then reports RPCA_ERR_TIMEOUT.  (The paper
+ * has no counterpart: this checks the library's failure path, not the method.) */
+int rpca_wait_selftest(int64_t limit_cycles, int64_t *waited_cycles, void *ws, size_t ws_bytes,
+                       rpca_stream_t stream);
 
 /* Wait for `stream`, then copy the device status word out of `ws` into *status. */
 int rpca_read_status(const void *ws, rpca_stream_t stream, int32_t *status);

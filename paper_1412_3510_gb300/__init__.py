@@ -10,4 +10,5 @@ from .rpca import (RpcaError, rpca_dense, rpca_dense_workspace_size, rpca_gaussi
                    read_status_block, workspace, rpca_timing_enable, rpca_timing_reset,
                    rpca_timing_read, rpca_timing_select, rpca_sketch_features, rpca_batched_features, batch_col_offsets,
                    rpca_mlp_pack, rpca_mlp_forward, rpca_mlp_loss_grad, rpca_mlp_adam, rpca_leverage_target,
-                   rpca_dense_learned, weights_table, rpca_batched_tune, rpca_sym, rpca_nystrom, rpca_small_svd)
+                   rpca_dense_learned, weights_table, rpca_batched_tune, rpca_sym, rpca_nystrom, rpca_small_svd,
+                   rpca_batched_learned)

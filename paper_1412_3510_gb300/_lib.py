@@ -62,6 +62,8 @@ SIGNATURES = [
     ("rpca_batched", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P]),
     ("rpca_batched_tune", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _P, _P, _SZ, _P, C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    ("rpca_batched_learned_workspace_size", _SZ, [_I32, _I64, _I64, _OPTS]),
+    ("rpca_batched_learned", C.c_int, [_I32, _P, _I64, _I64, _OPTS, _P, _I32, C.c_float, _P, _P, _P, _SZ, _P]),
     ("rpca_features_workspace_size", _SZ, [_I64, _I64]),
     ("rpca_sketch_features", C.c_int, [_P, _I64, _I64, _I64, _I32, _U64, _P, _P, _SZ, _P]),
     ("rpca_batched_features_workspace_size", _SZ, [_I64]),
@@ -80,6 +82,7 @@ SIGNATURES = [
     ("rpca_small_svd", C.c_int, [_P, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("rpca_gaussian_omega", C.c_int, [_I64, _I32, _U64, _U64, _P, _I64, _P]),
     ("rpca_philox4x64_10", C.c_int, [_U64, _U64, _U64, _I64, _P, _P]),
+    ("rpca_wait_selftest", C.c_int, [_I64, C.POINTER(C.c_int64), _P, _SZ, _P]),
     ("rpca_read_status", C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
     ("rpca_status_string", C.c_char_p, [C.c_int]),
     ("rpca_launch_count", C.c_int64, []),

@@ -41,9 +41,11 @@ __global__ void __launch_bounds__(256) order_kernel(const Item *__restrict__ ite
 }
 
 __global__ void check_items_kernel(const Item *__restrict__ items, int count, int l, int k, int64_t max_m,
-                                   int32_t *__restrict__ item_status, int *__restrict__ queue, DevStatus *st) {
+                                   int32_t *__restrict__ item_status, const int32_t *__restrict__ active,
+                                   int *__restrict__ queue, DevStatus *st) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        if (active && active[i] == 0) continue;                            // skipped: status untouched
         const bool ok = item_ok(items[i], l, k, max_m);
         if (item_status) item_status[i] = ok ? 1 : RPCA_ERR_INVALID_ARG;     // 1: pending
         if (!ok) dev_fail(st, RPCA_ERR_INVALID_ARG);
@@ -115,8 +117,13 @@ int check_args(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t
     return RPCA_OK;
 }
 
+}  // namespace
+
+namespace rpca {
+
 int run_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, const rpca_opts *o,
-                const float *const *col_weights, int32_t *item_status, void *ws, cudaStream_t s, int shape) {
+                const float *const *col_weights, int32_t *item_status, void *ws, cudaStream_t s, int shape,
+                const int32_t *active, float *sk1) {
     static_assert(sizeof(rpca_mat_desc) == sizeof(rpca::Item), "descriptor layout");
     const BatchLayout B = batch_layout(count, max_m, o->l);
     char *base = reinterpret_cast<char *>(ws);
@@ -126,12 +133,13 @@ int run_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, const 
     auto *items = reinterpret_cast<const rpca::Item *>(descs);
     if (cudaMemsetAsync(st, 0, sizeof(rpca::DevStatus), s) != cudaSuccess) return RPCA_ERR_CUDA;
     rpca::check_items_kernel<<<(int)rpca::cdiv(count, 256), 256, 0, s>>>(items, count, o->l, o->k, max_m, item_status,
-                                                                         queue, st);
+                                                                         active, queue, st);
     RPCA_CHECK_LAUNCH();
     rpca::order_kernel<<<(int)rpca::cdiv(count, 256), 256, 0, s>>>(items, count, order);
     RPCA_CHECK_LAUNCH();
-    rpca::BatchLaunch a{items, order, count, o->l, o->k, o->its, o->raw, o->seed, col_weights, item_status, queue,
-                        reinterpret_cast<float *>(base + B.slots), B.slot_floats, max_m, rpca::num_sms(), s};
+    rpca::BatchLaunch a{items, order, count, o->l, o->k, o->its, o->raw, o->seed, col_weights, item_status, active,
+                        sk1, queue, reinterpret_cast<float *>(base + B.slots), B.slot_floats, max_m, rpca::num_sms(),
+                        s};
     switch (shape) {
         case 0: return rpca::launch_batched_r2k64(a);
         case 2: return rpca::launch_batched_r8k32(a);
@@ -139,15 +147,24 @@ int run_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, const 
     }
 }
 
-}  // namespace
+int batched_shape(int32_t count, int64_t max_m, int64_t max_n, const rpca_opts *o) {
+    return tuned_rpt(tune_key(count, max_m, max_n, o));
+}
+
+int check_batched_args(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n, const rpca_opts *o,
+                       const void *ws, size_t ws_bytes) {
+    return check_args(count, descs, max_m, max_n, o, ws, ws_bytes);
+}
+
+}  // namespace rpca
 
 extern "C" int rpca_batched(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n,
                             const rpca_opts *o, const float *const *col_weights, int32_t *item_status, void *ws,
                             size_t ws_bytes, rpca_stream_t stream) {
     RPCA_TRY(check_args(count, descs, max_m, max_n, o, ws, ws_bytes));
     if (count == 0) return RPCA_OK;
-    return run_batched(count, descs, max_m, o, col_weights, item_status, ws, (cudaStream_t)stream,
-                       tuned_rpt(tune_key(count, max_m, max_n, o)));
+    return rpca::run_batched(count, descs, max_m, o, col_weights, item_status, ws, (cudaStream_t)stream,
+                             tuned_rpt(tune_key(count, max_m, max_n, o)), nullptr, nullptr);
 }
 
 extern "C" int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int64_t max_m, int64_t max_n,
@@ -164,10 +181,10 @@ extern "C" int rpca_batched_tune(int32_t count, const rpca_mat_desc *descs, int6
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return RPCA_ERR_CUDA; }
     int rc = RPCA_OK;
     for (int c = 0; c < kNumShapes && rc == RPCA_OK; ++c) {
-        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c);     // warm-up
+        rc = rpca::run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c, nullptr, nullptr);  // warm-up
         if (rc != RPCA_OK) break;
         if (cudaEventRecord(e0, s) != cudaSuccess) { rc = RPCA_ERR_CUDA; break; }
-        rc = run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c);
+        rc = rpca::run_batched(count, descs, max_m, o, col_weights, item_status, ws, s, c, nullptr, nullptr);
         if (rc != RPCA_OK) break;
         float t = 0.f;
         if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

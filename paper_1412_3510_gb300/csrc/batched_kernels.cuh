@@ -40,6 +40,8 @@ struct BatchLaunch {
     uint64_t seed;
     const float *const *weights;
     int32_t *item_status;
+    const int32_t *active;        // optional: items with active[i] == 0 are skipped (outputs untouched)
+    float *sk1;                   // optional: s_{k+1} of each item's rank-l approximation
     int *queue;
     float *slots;
     int64_t slot_floats, max_m;
@@ -509,7 +511,7 @@ __device__ void small_svd(Smem &sm, int l) {
 // Per item: the method.  Y0 / Y1: this CTA's m-side slots.
 template <int CPT, int RPT, int KB>
 __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its, int raw, uint64_t seed,
-                         const float *weights, float *Y0, int32_t *status) {
+                         const float *weights, float *Y0, int32_t *status, float *sk1_out) {
     const float *A = it.A;
     const int64_t m = it.m, n = it.n, lda = it.lda;
     float *mean = sm.vec + kMaxLP, *qsum = sm.vec + 2 * kMaxLP;
@@ -617,6 +619,7 @@ __device__ void run_item(Smem &sm, const Item &it, int l, int lp, int k, int its
         it.U[i * it.ldu + r] = sgn[r] * v;
     }
     for (int r = threadIdx.x; r < k; r += blockDim.x) it.S[r] = sm.sig[r];
+    if (threadIdx.x == 0 && sk1_out) *sk1_out = l > k ? sm.sig[k] : 0.f;     // s_{k+1} of the rank-l approximation
     if (threadIdx.x == 0 && status) *status = RPCA_OK;
     __syncthreads();
 }
@@ -632,7 +635,8 @@ template <int CPT, int RPT, int KB>
 __global__ void __launch_bounds__(kThreads, 1)
 batched_kernel(const Item *__restrict__ items, const int32_t *__restrict__ order, int count, int l, int k, int its,
                int raw, uint64_t seed, const float *const *__restrict__ weights, int32_t *__restrict__ item_status,
-               int *__restrict__ queue, float *__restrict__ slots, int64_t slot_floats, int64_t max_m) {
+               const int32_t *__restrict__ active, float *__restrict__ sk1, int *__restrict__ queue,
+               float *__restrict__ slots, int64_t slot_floats, int64_t max_m) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int lp = (int)round_up(l + 1, 8);
@@ -646,8 +650,9 @@ batched_kernel(const Item *__restrict__ items, const int32_t *__restrict__ order
         const int idx = order ? order[q] : q;
         const Item it = items[idx];
         if (!item_ok(it, l, k, max_m)) continue;          // reported by check_items_kernel
+        if (active && active[idx] == 0) continue;
         run_item<CPT, RPT, KB>(sm, it, l, lp, k, its, raw, seed, weights ? weights[idx] : nullptr, Y0,
-                      item_status ? item_status + idx : nullptr);
+                      item_status ? item_status + idx : nullptr, sk1 ? sk1 + idx : nullptr);
     }
 }
 
@@ -667,7 +672,8 @@ int launch_batched_rpt(const BatchLaunch &a) {
             return RPCA_ERR_CUDA;                                                                                 \
         batched_kernel<CPT, RPT, KB><<<a.grid, kThreads, smem, a.stream>>>(a.items, a.order, a.count, a.l, a.k, a.its, \
                                                                        a.raw, a.seed, a.weights, a.item_status,    \
-                                                                       a.queue, a.slots, a.slot_floats, a.max_m);  \
+                                                                       a.active, a.sk1, a.queue, a.slots,          \
+                                                                       a.slot_floats, a.max_m);                    \
     } while (0)
     if (lp <= 8) RPCA_BATCH_LAUNCH(1);
     else if (lp <= 16) RPCA_BATCH_LAUNCH(2);

@@ -35,11 +35,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: true when the phase completed, false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag,
+                                          long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try(b, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }

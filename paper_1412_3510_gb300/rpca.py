@@ -448,6 +448,39 @@ def rpca_batched(batch: Batch, l: int | None = None, its: int = 2, raw: bool = F
     return batch.U, batch.S, batch.V
 
 
+def rpca_batched_learned(batch: Batch, col_weights, l: int | None = None, its: int = 2, raw: bool = False,
+                         seed: int = 0, resid_iters: int = 3, fallback_ratio: float = 1.1,
+                         ws: torch.Tensor | None = None, est_out: torch.Tensor | None = None, stream=None,
+                         check: bool = True):
+    """Batched PCA with learned test-matrix weights and the per-matrix fallback to the
+    plain sketch (see include/rpca.h).  batch.status afterwards: 0 kept, 1 fell back.
+    Returns (U list, S list, V list, est) with est (count x 2, device): the learned
+    run's residual estimate and s_{k+1} per matrix."""
+    k = batch.k
+    opts = make_opts(k, l, its, raw, seed, "fp32", "cholqr")
+    lib = L.load()
+    count = len(batch.mats)
+    need = int(lib.rpca_batched_learned_workspace_size(count, batch.max_m, batch.max_n, C.byref(opts)))
+    if need == 0:
+        raise RpcaError(L.RPCA_ERR_INVALID_ARG, "rpca_batched_learned_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, batch.desc.device)
+    if isinstance(col_weights, torch.Tensor):
+        wptr = col_weights
+    else:
+        wptr = weights_table(col_weights, batch.desc.device)
+        batch._wkeep = (col_weights, wptr)
+    if est_out is None:
+        est_out = torch.empty(count, 2, dtype=torch.float32, device=batch.desc.device)
+    code = lib.rpca_batched_learned(count, _ptr(batch.desc), batch.max_m, batch.max_n, C.byref(opts), _ptr(wptr),
+                                    int(resid_iters), float(fallback_ratio), _ptr(batch.status), _ptr(est_out),
+                                    _ptr(ws), ws.numel(), _stream(stream))
+    _check(code, "rpca_batched_learned")
+    if check:
+        _check(rpca_read_status(ws, stream), "rpca_batched_learned (device)")
+    return batch.U, batch.S, batch.V, est_out
+
+
 def rpca_batched_tune(batch: Batch, l: int | None = None, its: int = 2, raw: bool = False, seed: int = 0,
                       col_weights=None, ws: torch.Tensor | None = None, stream=None):
     """Time the batched kernel's pass-tile shapes on this batch and keep the fastest for later

@@ -198,6 +198,51 @@ def test_dense_learned_fallback_fires():
     assert torch.equal(U, U2) and torch.equal(Sg, S2) and torch.equal(V, V2)
 
 
+def test_batched_learned_fallback_fires_per_matrix():
+    """The batched form's fallback: matrices whose learned weights hide the signal (weight
+    1e-2 on the 12 columns that carry the top-k subspace) are recomputed with the plain
+    sketch and flagged; matrices with neutral weights keep their result.  Both end equal,
+    bit for bit, to plain rpca_batched."""
+    torch = cuda()
+    import paper_1412_3510_gb300 as rp
+    k, l, its = 5, 11, 1
+    mats, weights, bad = [], [], []
+    for i in range(4):                                   # signal hidden by the weights
+        rng = np.random.default_rng(40 + i)
+        m, n = 500 + 37 * i, 300 - 11 * i
+        A = rng.standard_normal((m, n))
+        loud = rng.choice(n, 12, replace=False)
+        A[:, loud] += rng.standard_normal((m, 5)) @ rng.standard_normal((5, 12)) * 2.0
+        d = np.ones(n, dtype=np.float32)
+        d[loud] = 1e-2
+        mats.append(A.astype(np.float32))
+        weights.append(d)
+        bad.append(True)
+    for i in range(4):                                   # neutral weights, decaying spectra
+        A = S.kernel_matrix_np(S.KernelSpec(400 + 50 * i, 200 + 20 * i, 0.3 + 0.1 * i, 60 + i))
+        mats.append(A)
+        weights.append(np.ones(A.shape[1], dtype=np.float32))
+        bad.append(False)
+    dev = [to_dev(a) for a in mats]
+    wdev = [to_dev(d) for d in weights]
+    b1 = rp.Batch(dev, k)
+    U1, S1, V1, est = rp.rpca_batched_learned(b1, wdev, l, its=its, seed=3, resid_iters=3, fallback_ratio=1.1)
+    st = b1.status.cpu().numpy()
+    e = est.cpu().numpy()
+    assert np.array_equal(st, np.where(bad, 1, 0)), (st, e)
+    assert np.all(e[:4, 0] > 1.1 * e[:4, 1]) and np.all(e[4:, 0] <= 1.1 * e[4:, 1])
+    b2 = rp.Batch(dev, k)
+    U2, S2, V2 = rp.rpca_batched(b2, l, its=its, seed=3)
+    for i in range(len(mats)):
+        assert torch.equal(U1[i], U2[i]) and torch.equal(S1[i], S2[i]) and torch.equal(V1[i], V2[i]), i
+    # the estimate is Section 4's estimator: it never exceeds the residual's norm
+    for i in range(4, 8):
+        Ai = mats[i].astype(np.float64)
+        Ac = Ai - Ai.mean(0)
+        E = Ac - (to_np(U1[i]) * to_np(S1[i])) @ to_np(V1[i]).T
+        assert e[i, 0] <= np.linalg.norm(E, 2) * (1 + 1e-4)
+
+
 def test_dense_learned_rejects_bad_args():
     cuda()
     import paper_1412_3510_gb300 as rp
