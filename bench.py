@@ -567,6 +567,32 @@ def run_batched(args, w, dev, world, rank, barrier):
                "mode": "double-buffered: the upload of step i+1 overlaps step i; one copy each way per step"}
         del host, arena2, batch2, outs, sets
 
+    # the plain dense entry point looped over the same matrices (one rpca_dense call per
+    # matrix, eager launches on one stream, one workspace sized for the largest)
+    plain_loop = None
+    if not args.no_forms:
+        o_max = rp.make_opts(k, l, its, raw, seed=1 + rank)
+        ws_d = rp.workspace(max(rp.rpca_dense_workspace_size(sp.m, sp.n, o_max) for sp in specs), dev)
+        outs_d = [(batch.U[i], batch.S[i], batch.V[i]) for i in range(len(mats))]
+
+        def dense_loop():
+            for a, o_ in zip(mats, outs_d):
+                rp.rpca_dense(a, k, l, its=its, raw=raw, seed=1 + rank, ws=ws_d, out=o_, check=False)
+        dense_loop()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            dense_loop()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1) / reps
+        plain_loop = {"value": len(mats) / (ms_loop / 1e3), "ms_per_batch": ms_loop, "its": its,
+                      "how": "rpca_dense per matrix, eager launches on one stream",
+                      "batched_speedup": ms_loop / ms_step}
+        del ws_d
+
     learned = None if args.no_learned else learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream)
 
     cpu = None
@@ -594,6 +620,7 @@ def run_batched(args, w, dev, world, rank, barrier):
                    "tile_autotune": tuning,
                    "parallelism": f"replicas x{world}"},
         "gbs_per_pass": achieved, "its_sweep_pca_per_s": {str(kk): v for kk, v in sweep.items()} | {str(its): value},
+        "forms": {"plain_dense_loop": plain_loop},
         "accuracy": {"sample": int(ratios.size), "resid_over_sigma_k1_median": float(np.median(ratios)),
                      "resid_over_sigma_k1_max": float(ratios.max()),
                      "fraction_resid_ok": float(np.mean(ratios <= 1.1)), "status": status, "bad_items": item_bad},
@@ -681,6 +708,29 @@ def learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream):
             ms = timed(g, steps) / steps
             speed[f"{name}_its{its}"] = len(mats) / (ms / 1e3)
             del g
+    # the learned sketch with the per-matrix fallback (3-iteration Section 4 estimate,
+    # plain-sketch rerun of the matrices whose estimate exceeds 1.1 s_{k+1})
+    fb = {}
+    lws = rp.workspace(int(LIB.load().rpca_batched_learned_workspace_size(
+        len(mats), batch.max_m, batch.max_n, rp.make_opts(k, l, 2, raw))), dev)
+    for its_f in (1, 2):
+        weights()
+        rp.rpca_batched_learned(batch, wtab, l, its=its_f, raw=raw, seed=seed, resid_iters=3, ws=lws)
+        fell = int((batch.status == 1).sum().item())
+        acc_f = summary(ratios())
+        for _ in range(args.warmup):
+            weights()
+            rp.rpca_batched_learned(batch, wtab, l, its=its_f, raw=raw, seed=seed, resid_iters=3, ws=lws,
+                                    check=False)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            weights()
+            rp.rpca_batched_learned(batch, wtab, l, its=its_f, raw=raw, seed=seed, resid_iters=3, ws=lws,
+                                    check=False)
+        ms = timed(g, steps) / steps
+        fb[f"its{its_f}"] = {"pca_per_s": len(mats) / (ms / 1e3), "fell_back": fell, "accuracy": acc_f}
+        del g
     for _ in range(args.warmup):
         weights()
     torch.cuda.synchronize()
@@ -697,7 +747,9 @@ def learned_ab(args, w, dev, rank, batch, mats, ws, timed, stream):
             "sigma_k1": "exact (FP64 svdvals of the centred matrix)",
             "accuracy": acc, "pca_per_s": speed, "gpu_launches_per_step": launches,
             "weights_ms_per_batch": w_ms,
-            "fallback": "dense entry point only (rpca_dense_learned); the batched form reports accuracy"}
+            "with_fallback": fb,
+            "fallback": ("rpca_batched_learned: 3-iteration Section 4 estimate per matrix, plain-sketch rerun "
+                         "when it exceeds 1.1 s_{k+1}")}
 
 
 def error_vs_fp64(A, k, l, its, raw, seed, iters, ws, U, S, V):

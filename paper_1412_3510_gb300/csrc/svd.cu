@@ -105,10 +105,10 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
             }
             // the rotation that zeroes c (Rutishauser's formulas).  Only its orthogonality
             // matters: the angle t may carry fast-intrinsic error, but cs = 1 / sqrt(1 + t^2)
-            // is formed with the correctly rounded square root and division, so that
-            // cs^2 + sn^2 = 1 to unbiased rounding -- an approximate reciprocal square root
-            // shrinks both columns by ~1e-8 per rotation, a systematic drift of the column
-            // norms (the singular values) over the hundreds of rotations a column takes
+            // is the approximate reciprocal square root refined by one Newton step, so that
+            // cs^2 + sn^2 = 1 to unbiased rounding -- the unrefined approximation shrinks both
+            // columns by ~1e-8 per rotation, a systematic drift of the column norms (the
+            // singular values) over the hundreds of rotations a column takes
             float cs = 1.f, sn = 0.f;
             const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
             if (mu > tol) {
@@ -118,7 +118,8 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                 mu_max = fmaxf(mu_max, delta > 0.f ? fminf(mu * mu / delta, 1.f) : 1.f);
                 const float zeta = __fdividef(b - a, 2.f * c);
                 const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-                cs = 1.f / sqrtf(fmaf(t, t, 1.f));
+                const float q = fmaf(t, t, 1.f), y0 = rsqrtf(q);
+                cs = y0 * fmaf(-0.5f * q * y0, y0, 1.5f);     // one Newton step on rsqrt
                 sn = cs * t;
                 if (CACHE > 0) {
 #pragma unroll

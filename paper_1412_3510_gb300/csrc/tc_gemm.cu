@@ -11,7 +11,7 @@
 // of A for A X; (column tile, K split) pairs for A^T Q), all N <= 256 output
 // columns per tile:
 //   warp 0       TMA loads of FP32 A stages (128B-swizzled 32-column boxes),
-//                a ring of up to eight stages (what shared memory leaves)
+//                3-stage ring
 //   warp 2       bulk copies of the pre-split BF16 block-operand stages
 //   warps 8..15  split each FP32 stage into BF16 hi/lo in the MMA's canonical
 //                K-major layout (transposing for A^T); the swizzle keeps these
@@ -47,31 +47,22 @@ constexpr int kBM = 128;              // MMA M and CTA output rows
 // therefore covers at most kChunkRows of K; the epilogue adds the chunks of a tile
 // in FP32 with round-to-nearest, which bounds the drift near 1.5e-5.
 constexpr int kChunkRows = 2048;
-constexpr int kMaxStagesA = 8;        // FP32 A ring depth, at most
+constexpr int kStagesA = 3;           // FP32 A ring depth
 constexpr int kBufs = 2;              // converted BF16 buffers
-// Dynamic shared memory a CTA plans for (the launch adds 1 KB of alignment slack; the
-// sm_103a limit is 227 KB).
-constexpr uint32_t kSmemBudget = 220u * 1024u;
 
 // Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).  NS BF16
-// pieces per operand; GRAM: the B operand is the A operand (no B buffers).  The FP32
-// ring takes what the two converted buffers leave (2..8 stages): a pass streams A at
-// the rate the bytes in flight per SM allow over the memory latency, so the deepest
-// ring that fits is used (BK = 32: eight 16 KB stages).
+// pieces per operand; GRAM: the B operand is the A operand (no B buffers).
 template <int BK, int NS, bool GRAM>
 struct Plan {
     static constexpr uint32_t a32_bytes = kBM * BK * 4;          // FP32 stage
     static constexpr uint32_t abf_bytes = kBM * BK * 2;          // one piece of A
     uint32_t b_bytes;                                            // one piece of B (N x BK bf16)
-    uint32_t stages_a, off_a32, off_buf, buf_bytes, off_bar, total;
+    uint32_t off_a32, off_buf, buf_bytes, off_bar, total;
     __host__ __device__ explicit Plan(int N) {
         b_bytes = GRAM ? 0u : (uint32_t)N * BK * 2;
-        buf_bytes = NS * abf_bytes + NS * b_bytes;
-        const uint32_t fixed = kBufs * buf_bytes + 256;
-        const uint32_t room = fixed < kSmemBudget ? (kSmemBudget - fixed) / a32_bytes : 0;
-        stages_a = room < 2 ? 2u : (room > (uint32_t)kMaxStagesA ? (uint32_t)kMaxStagesA : room);
         off_a32 = 0;
-        off_buf = stages_a * a32_bytes;
+        off_buf = kStagesA * a32_bytes;
+        buf_bytes = NS * abf_bytes + NS * b_bytes;
         off_bar = off_buf + kBufs * buf_bytes;
         total = off_bar + 256;
     }
@@ -110,10 +101,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const Plan<BK, NS, GRAM> P(args.N);
-    const int SA = (int)P.stages_a;
     uint64_t *full_a = reinterpret_cast<uint64_t *>(smem + P.off_bar);
-    uint64_t *empty_a = full_a + kMaxStagesA;
-    uint64_t *full_c = empty_a + kMaxStagesA;
+    uint64_t *empty_a = full_a + kStagesA;
+    uint64_t *full_c = empty_a + kStagesA;
     uint64_t *empty_c = full_c + kBufs;
     uint64_t *tm_full = empty_c + kBufs;
     uint64_t *tm_empty = tm_full + 2;
@@ -126,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     const uint32_t tmem_cols = 2 * acc_cols;                  // two accumulators
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
+        for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
         for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM ? 0 : 1)); mbar_init(&empty_c[b], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tm_full[a], 1); mbar_init(&tm_empty[a], 4); }
         *abort_flag = 0;
@@ -170,8 +160,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 int nst;
                 tile_info(t, row0, kbeg, nst);
                 for (int k = 0; k < nst && ok; ++k, ++g) {
-                    const int s = (int)(g % SA);
-                    if (g >= (uint32_t)SA && !mbar_wait(&empty_a[s], ((g / SA) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    const int s = g % kStagesA;
+                    if (g >= kStagesA && !mbar_wait(&empty_a[s], ((g / kStagesA) & 1) ^ 1, abort_flag)) { fail(); break; }
                     uint8_t *dst = smem + P.off_a32 + s * P.a32_bytes;
                     mbar_arrive_tx(&full_a[s], P.a32_bytes);
                     const int64_t kk = kbeg + (int64_t)k * BK;
@@ -318,8 +308,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             int nst;
             tile_info(t, row0, kbeg, nst);
             for (int k = 0; k < nst && ok; ++k, ++g) {
-                const int s = (int)(g % SA), b = g % kBufs;
-                if (!mbar_wait(&full_a[s], (g / SA) & 1, abort_flag)) { fail(); break; }
+                const int s = g % kStagesA, b = g % kBufs;
+                if (!mbar_wait(&full_a[s], (g / kStagesA) & 1, abort_flag)) { fail(); break; }
                 if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
                 const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
                 uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
@@ -478,8 +468,7 @@ int launch_pass(const CUtensorMap &map, const TcArgs &a, dim3 grid, cudaStream_t
 }  // namespace
 
 int tc_n(int lp) { return (int)round_up(lp, 16); }
-// K per pass stage: 32 rows of A (16 KB of FP32), so that eight stages fit in flight
-int tc_bk(int lp) { (void)lp; return 32; }
+int tc_bk(int lp) { return tc_n(lp) <= 128 ? 64 : 32; }
 
 bool tc_supported(const float *A, int64_t lda, int lp) {
     return tc_n(lp) <= 256 && (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && lda % 4 == 0;
