@@ -112,10 +112,11 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
             float cs = 1.f, sn = 0.f;
             const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
             if (mu > tol) {
-                // by quadratic convergence the next sweep's measure for this pair is about
-                // mu^2 / delta, delta the relative gap of the two squared column norms
+                // by quadratic convergence the next sweep's largest measure is bounded by
+                // about l mu^2 / delta (the off-diagonal mass of the whole sweep over the
+                // relative gap delta of the pair's squared column norms)
                 const float delta = fabsf(b - a) / (a + b);
-                mu_max = fmaxf(mu_max, delta > 0.f ? fminf(mu * mu / delta, 1.f) : 1.f);
+                mu_max = fmaxf(mu_max, delta > 0.f ? fminf((float)l * mu * mu / delta, 1.f) : 1.f);
                 const float zeta = __fdividef(b - a, 2.f * c);
                 const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
                 const float q = fmaf(t, t, 1.f), y0 = rsqrtf(q);

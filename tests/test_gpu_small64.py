@@ -70,9 +70,12 @@ def test_dense_small_fp64_parity(m, n, k, l, its, raw, precision):
     Uo, so, Vo = O.rpca(A, k, l, its, raw=raw, seed=4)
     _check(to_np(U), to_np(Sg), Uo, so, k)
     _check(to_np(V), to_np(Sg), Vo, so, k)
-    # the same PCA with the FP32 l x l path agrees to the FP32 noise of the passes
+    # the same PCA with the FP32 l x l path agrees to the noise of the passes: FP32 FFMA, or
+    # 16 significant bits per factor in the split-BF16 form (the two runs' blocks differ in
+    # their last bits, and so do their BF16 splits)
     _, S32, _ = rp.rpca_dense(to_dev(A), k, l, its=its, raw=raw, seed=4, precision=precision)
-    assert np.all(np.abs(to_np(Sg) - to_np(S32)) <= 2e-5 * to_np(S32) + 2e-6 * so[0])
+    rtol = 2e-5 if precision == "fp32" else 6e-5
+    assert np.all(np.abs(to_np(Sg) - to_np(S32)) <= rtol * to_np(S32) + 2e-6 * so[0])
 
 
 def test_csr_sym_nystrom_small_fp64_parity():
