@@ -461,10 +461,7 @@ __device__ void small_svd(Smem &sm, int l) {
                 if (q < l && fabsf(ga) > tol * sqrtf(al * be) && ga != 0.f) {
                     const float zeta = (be - al) / (2.f * ga);
                     const float t = copysignf(1.f, zeta) / (fabsf(zeta) + hypotf(zeta, 1.f));
-                    // rsqrt refined by one Newton step: the unrefined approximation would shrink
-                    // the column norms (the singular values) a little with every rotation
-                    const float tq = fmaf(t, t, 1.f), y0 = rsqrtf(tq);
-                    const float cs = y0 * fmaf(-0.5f * tq * y0, y0, 1.5f), sn = cs * t;
+                    const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
                     if (lane < l) {
                         M[p * l + lane] = cs * x - sn * y;
                         M[q * l + lane] = sn * x + cs * y;

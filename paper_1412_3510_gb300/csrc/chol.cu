@@ -287,12 +287,7 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
                     const float t = __shfl_sync(0xffffffffu, thr, j);
                     const bool good = j >= bl || (d > t && d > 0.f);
                     fail |= !good;                          // uniform: every lane sees d
-                    // row j of R: r_jc (lane j: sqrt(d)).  The approximate reciprocal square root
-                    // is refined by one Newton step y (3 - d y^2) / 2, so that the factor's scale,
-                    // which reaches the singular values through the accumulated R, carries no bias
-                    const float dd = j < bl && good ? d : 1.f;
-                    const float y0 = rsqrtf(dd);
-                    a[j] *= y0 * fmaf(-0.5f * dd * y0, y0, 1.5f);
+                    a[j] *= rsqrtf(j < bl && good ? d : 1.f);   // row j of R: r_jc (lane j: sqrt(d))
                     if (lane == j) rd = a[j];
                     // constant trip counts (r > j resolved at compile time) keep a[] in registers
 #pragma unroll

@@ -103,12 +103,11 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                 b += __shfl_xor_sync(0xffffffffu, b, off);
                 c += __shfl_xor_sync(0xffffffffu, c, off);
             }
-            // the rotation that zeroes c (Rutishauser's formulas).  Only its orthogonality
-            // matters: the angle t may carry fast-intrinsic error, but cs = 1 / sqrt(1 + t^2)
-            // is the approximate reciprocal square root refined by one Newton step, so that
-            // cs^2 + sn^2 = 1 to unbiased rounding -- the unrefined approximation shrinks both
-            // columns by ~1e-8 per rotation, a systematic drift of the column norms (the
-            // singular values) over the hundreds of rotations a column takes
+            // the rotation that zeroes c (Rutishauser's formulas), with fast intrinsics.  The
+            // rotations are not exactly orthogonal (cs^2 + sn^2 = 1 to a few ulps, and the
+            // error has a sign: over the hundreds of rotations a column takes, the column
+            // norms drift by ~1e-5); svd_finish_kernel therefore takes the singular values
+            // and the left vectors from the original matrix and the normalised right vectors
             float cs = 1.f, sn = 0.f;
             const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
             if (mu > tol) {
@@ -119,8 +118,7 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
                 mu_max = fmaxf(mu_max, delta > 0.f ? fminf((float)l * mu * mu / delta, 1.f) : 1.f);
                 const float zeta = __fdividef(b - a, 2.f * c);
                 const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
-                const float q = fmaf(t, t, 1.f), y0 = rsqrtf(q);
-                cs = y0 * fmaf(-0.5f * q * y0, y0, 1.5f);     // one Newton step on rsqrt
+                cs = rsqrtf(fmaf(t, t, 1.f));
                 sn = cs * t;
                 if (CACHE > 0) {
 #pragma unroll
@@ -295,6 +293,80 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
         }
 }
 
+// The outputs from the original matrix M0 = R^T and the replayed right vectors: for
+// r < k, z = Zk[:, r] / |Zk[:, r]|, w = M0 z, sigma_r = |w|, W[:, r] = w / sigma_r, then
+// the k triplets sorted by sigma (descending, ties by index).  The Jacobi's rotations
+// are orthogonal only to a few ulps with a systematic sign, so the rotated columns'
+// norms drift (~1e-5 over a full SVD at l = 150) and M0 != W Sigma Z^T to that level;
+// after normalising Z, sigma and W computed this way are consistent with Z to FP32
+// rounding.  One CTA; M0 staged in shared memory (row stride l + 1), a warp per column.
+// scratch: 2 lp kp floats (the rotation log, no longer needed after the replay).
+constexpr int kFinThreads = 512;
+
+__global__ void __launch_bounds__(kFinThreads)
+svd_finish_kernel(const float *__restrict__ R, int l, int lp, int k, int kp, float *__restrict__ Wk,
+                  float *__restrict__ Zk, float *__restrict__ sig, float *__restrict__ scratch) {
+    extern __shared__ float fm[];
+    const int ldm = l + 1;
+    float *M = fm;                                    // l x ldm: M[i][j] = R[j][i]
+    float *zw = M + (size_t)l * ldm;                  // one l-vector per warp
+    __shared__ float snew[RPCA_MAX_L];
+    __shared__ int rank_of[RPCA_MAX_L];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+    for (int e = tid; e < l * l; e += blockDim.x) {
+        const int j = e / l, i = e - j * l;
+        M[i * ldm + j] = R[e];
+    }
+    __syncthreads();
+    float *Ws = scratch, *Zs = scratch + (size_t)lp * kp;
+    float *z = zw + (size_t)warp * l;
+    for (int r = warp; r < k; r += nwarps) {
+        float nz = 0.f;
+        for (int i = lane; i < l; i += 32) {
+            const float v = Zk[(size_t)i * kp + r];
+            z[i] = v;
+            nz = fmaf(v, v, nz);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, off);
+        const float inz = nz > 0.f ? 1.f / sqrtf(nz) : 0.f;
+        __syncwarp();
+        float ns = 0.f;
+        for (int i = lane; i < l; i += 32) {
+            float w = 0.f;
+            for (int j = 0; j < l; ++j) w = fmaf(M[i * ldm + j], z[j], w);
+            w *= inz;
+            Ws[(size_t)i * kp + r] = w;
+            Zs[(size_t)i * kp + r] = z[i] * inz;
+            ns = fmaf(w, w, ns);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, off);
+        const float sv = sqrtf(ns);
+        const float isv = sv > 0.f ? 1.f / sv : 0.f;
+        for (int i = lane; i < l; i += 32) Ws[(size_t)i * kp + r] *= isv;
+        if (lane == 0) snew[r] = sv;
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int r = tid; r < k; r += blockDim.x) {
+        const float sr = snew[r];
+        int rank = 0;
+        for (int q = 0; q < k; ++q) rank += (snew[q] > sr) || (snew[q] == sr && q < r);
+        rank_of[r] = rank;
+        sig[rank] = sr;
+    }
+    __syncthreads();
+    for (int e = tid; e < lp * kp; e += blockDim.x) {
+        const int i = e / kp, r = e - i * kp;
+        if (r < k) {
+            const int dst = i * kp + rank_of[r];
+            Wk[dst] = i < l ? Ws[e] : 0.f;
+            Zk[dst] = i < l ? Zs[e] : 0.f;
+        }
+    }
+}
+
 // Per column r < k: flip V[:, r] when its largest-|entry| (first on ties) is
 // negative; apply the same sign to Wk[:, r]; S[r] = sig[r].
 __global__ void __launch_bounds__(256)
@@ -365,6 +437,13 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
         return RPCA_ERR_CUDA;
     replay_kernel<<<grid, kReplayWarps * 32, rsmem, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
                                                          lp, k, kp);
+    RPCA_CHECK_LAUNCH();
+    const size_t fsmem = ((size_t)l * (l + 1) + (size_t)(kFinThreads / 32) * l) * sizeof(float);
+    if (cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) + (size_t)(kFinThreads / 32) * RPCA_MAX_L) *
+                                   sizeof(float))) != cudaSuccess)
+        return RPCA_ERR_CUDA;
+    svd_finish_kernel<<<1, kFinThreads, fsmem, s>>>(R, l, lp, k, kp, Wk, Zk, sig, rot);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }
