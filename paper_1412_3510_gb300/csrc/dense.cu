@@ -19,14 +19,17 @@ struct DenseOp final : Operator {
     bool tc(int lp) const { return precision == RPCA_PREC_BF16X3 && tc_supported(A, lda, lp); }
     size_t scratch_bytes(int lp) const override {
         if (precision != RPCA_PREC_BF16X3) return 0;
-        return std::max(tc_split_bytes(n, lp), tc_split_bytes(m, lp));
+        return std::max(apply_tail_offset(lp) + tc_apply_tail_bytes(lp), tc_split_bytes(m, lp));
     }
+    // A X's scratch: the split X, then the K pieces of the last wave's row tiles
+    size_t apply_tail_offset(int lp) const { return (tc_split_bytes(n, lp) + 255) & ~(size_t)255; }
     int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *bias) const override {
         if (tc(lp)) {
             auto *xs = reinterpret_cast<__nv_bfloat16 *>(scratch);
             RPCA_TRY(launch_tc_split(X, n, lp, xs, s));
             TimedScope ts(kTimeApplyKernel, s);
-            return launch_tc_apply(A, m, n, lda, xs, lp, Y, st, s, bias);
+            float *tail = reinterpret_cast<float *>(reinterpret_cast<char *>(scratch) + apply_tail_offset(lp));
+            return launch_tc_apply(A, m, n, lda, xs, lp, Y, st, s, bias, tail);
         }
         TimedScope ts(kTimeApplyKernel, s);
         return launch_sgemm(false, m, lp, n, A, lda, X, lp, Y, lp, 1, 0, s, nullptr, bias);

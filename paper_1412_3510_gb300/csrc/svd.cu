@@ -106,8 +106,8 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
             // the rotation that zeroes c (Rutishauser's formulas), with fast intrinsics.  The
             // rotations are not exactly orthogonal (cs^2 + sn^2 = 1 to a few ulps, and the
             // error has a sign: over the hundreds of rotations a column takes, the column
-            // norms drift by ~1e-5); svd_finish_kernel therefore takes the singular values
-            // and the left vectors from the original matrix and the normalised right vectors
+            // norms drift by ~1e-5); the replayed Z drifts by the same factors, and
+            // svd_finish_kernel divides it out
             float cs = 1.f, sn = 0.f;
             const float mu = valid ? fabsf(c) * rsqrtf(a) * rsqrtf(b) : 0.f;   // NaN when a b = 0
             if (mu > tol) {
@@ -293,60 +293,32 @@ replay_kernel(const float2 *__restrict__ rot, const int *__restrict__ sweeps_ptr
         }
 }
 
-// The outputs from the original matrix M0 = R^T and the replayed right vectors: for
-// r < k, z = Zk[:, r] / |Zk[:, r]|, w = M0 z, sigma_r = |w|, W[:, r] = w / sigma_r, then
-// the k triplets sorted by sigma (descending, ties by index).  The Jacobi's rotations
-// are orthogonal only to a few ulps with a systematic sign, so the rotated columns'
-// norms drift (~1e-5 over a full SVD at l = 150) and M0 != W Sigma Z^T to that level;
-// after normalising Z, sigma and W computed this way are consistent with Z to FP32
-// rounding.  One CTA; M0 staged in shared memory (row stride l + 1), a warp per column.
-// scratch: 2 lp kp floats (the rotation log, no longer needed after the replay).
+// The rotation-norm correction.  The Jacobi's rotations are orthogonal only to a
+// few ulps with a systematic sign, so every rotation scales the two columns it
+// mixes by the same factor in the rotated M and in the replayed Z (~1e-5 over a
+// full SVD at l = 150).  Column r of M J and of Z = J carry the same factor, so
+// sigma_r = |(M J)_r| / |Z_r| and Z_r / |Z_r| remove it while W (a direction) is
+// unchanged; the one-sided Jacobi's relative accuracy on small singular values is
+// kept.  The k triplets are then re-sorted (descending, ties by index).
+// One CTA; scratch: 2 lp kp floats (the rotation log, no longer needed after the replay).
 constexpr int kFinThreads = 512;
 
 __global__ void __launch_bounds__(kFinThreads)
-svd_finish_kernel(const float *__restrict__ R, int l, int lp, int k, int kp, float *__restrict__ Wk,
-                  float *__restrict__ Zk, float *__restrict__ sig, float *__restrict__ scratch) {
-    extern __shared__ float fm[];
-    const int ldm = l + 1;
-    float *M = fm;                                    // l x ldm: M[i][j] = R[j][i]
-    float *zw = M + (size_t)l * ldm;                  // one l-vector per warp
-    __shared__ float snew[RPCA_MAX_L];
+svd_finish_kernel(int l, int lp, int k, int kp, float *__restrict__ Wk, float *__restrict__ Zk,
+                  float *__restrict__ sig, float *__restrict__ scratch) {
+    __shared__ float snew[RPCA_MAX_L], inz[RPCA_MAX_L];
     __shared__ int rank_of[RPCA_MAX_L];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-    for (int e = tid; e < l * l; e += blockDim.x) {
-        const int j = e / l, i = e - j * l;
-        M[i * ldm + j] = R[e];
-    }
-    __syncthreads();
-    float *Ws = scratch, *Zs = scratch + (size_t)lp * kp;
-    float *z = zw + (size_t)warp * l;
     for (int r = warp; r < k; r += nwarps) {
         float nz = 0.f;
-        for (int i = lane; i < l; i += 32) {
-            const float v = Zk[(size_t)i * kp + r];
-            z[i] = v;
-            nz = fmaf(v, v, nz);
-        }
+        for (int i = lane; i < l; i += 32) nz = fmaf(Zk[(size_t)i * kp + r], Zk[(size_t)i * kp + r], nz);
 #pragma unroll
         for (int off = 16; off; off >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, off);
-        const float inz = nz > 0.f ? 1.f / sqrtf(nz) : 0.f;
-        __syncwarp();
-        float ns = 0.f;
-        for (int i = lane; i < l; i += 32) {
-            float w = 0.f;
-            for (int j = 0; j < l; ++j) w = fmaf(M[i * ldm + j], z[j], w);
-            w *= inz;
-            Ws[(size_t)i * kp + r] = w;
-            Zs[(size_t)i * kp + r] = z[i] * inz;
-            ns = fmaf(w, w, ns);
+        if (lane == 0) {
+            const float f = nz > 0.f ? 1.f / sqrtf(nz) : 0.f;
+            inz[r] = f;
+            snew[r] = nz > 0.f ? sig[r] * f : sig[r];
         }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, off);
-        const float sv = sqrtf(ns);
-        const float isv = sv > 0.f ? 1.f / sv : 0.f;
-        for (int i = lane; i < l; i += 32) Ws[(size_t)i * kp + r] *= isv;
-        if (lane == 0) snew[r] = sv;
-        __syncwarp();
     }
     __syncthreads();
     for (int r = tid; r < k; r += blockDim.x) {
@@ -354,15 +326,21 @@ svd_finish_kernel(const float *__restrict__ R, int l, int lp, int k, int kp, flo
         int rank = 0;
         for (int q = 0; q < k; ++q) rank += (snew[q] > sr) || (snew[q] == sr && q < r);
         rank_of[r] = rank;
-        sig[rank] = sr;
     }
     __syncthreads();
+    float *Ws = scratch, *Zs = scratch + (size_t)lp * kp;
+    for (int e = tid; e < lp * kp; e += blockDim.x) {
+        Ws[e] = Wk[e];
+        Zs[e] = Zk[e];
+    }
+    __syncthreads();
+    for (int r = tid; r < k; r += blockDim.x) sig[rank_of[r]] = snew[r];
     for (int e = tid; e < lp * kp; e += blockDim.x) {
         const int i = e / kp, r = e - i * kp;
         if (r < k) {
             const int dst = i * kp + rank_of[r];
-            Wk[dst] = i < l ? Ws[e] : 0.f;
-            Zk[dst] = i < l ? Zs[e] : 0.f;
+            Wk[dst] = Ws[e];
+            Zk[dst] = Zs[e] * inz[r];
         }
     }
 }
@@ -438,12 +416,7 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
     replay_kernel<<<grid, kReplayWarps * 32, rsmem, s>>>(reinterpret_cast<const float2 *>(rot), sweeps, l, perm, Zk,
                                                          lp, k, kp);
     RPCA_CHECK_LAUNCH();
-    const size_t fsmem = ((size_t)l * (l + 1) + (size_t)(kFinThreads / 32) * l) * sizeof(float);
-    if (cudaFuncSetAttribute(svd_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((size_t)RPCA_MAX_L * (RPCA_MAX_L + 1) + (size_t)(kFinThreads / 32) * RPCA_MAX_L) *
-                                   sizeof(float))) != cudaSuccess)
-        return RPCA_ERR_CUDA;
-    svd_finish_kernel<<<1, kFinThreads, fsmem, s>>>(R, l, lp, k, kp, Wk, Zk, sig, rot);
+    svd_finish_kernel<<<1, kFinThreads, 0, s>>>(l, lp, k, kp, Wk, Zk, sig, rot);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

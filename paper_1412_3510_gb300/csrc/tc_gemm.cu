@@ -49,10 +49,20 @@ constexpr int kBM = 128;              // MMA M and CTA output rows
 constexpr int kChunkRows = 2048;
 constexpr int kStagesA = 3;           // FP32 A ring depth
 constexpr int kBufs = 2;              // converted BF16 buffers
+// A in tensor memory (AT): the converted pieces of A leave shared memory, which then
+// holds a deeper FP32 ring (more bytes of A in flight per SM)
+constexpr int kStagesAT = 5;
+constexpr int kBufsAT = 2;
+template <bool AT>
+struct Ring {
+    static constexpr int stages = AT ? kStagesAT : kStagesA;
+    static constexpr int bufs = AT ? kBufsAT : kBufs;
+};
 
 // Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).  NS BF16
-// pieces per operand; GRAM: the B operand is the A operand (no B buffers).
-template <int BK, int NS, bool GRAM>
+// pieces per operand; GRAM: the B operand is the A operand (no B buffers); AT: the
+// pieces of A are in tensor memory (buffers hold B only).
+template <int BK, int NS, bool GRAM, bool AT = false>
 struct Plan {
     static constexpr uint32_t a32_bytes = kBM * BK * 4;          // FP32 stage
     static constexpr uint32_t abf_bytes = kBM * BK * 2;          // one piece of A
@@ -61,9 +71,9 @@ struct Plan {
     __host__ __device__ explicit Plan(int N) {
         b_bytes = GRAM ? 0u : (uint32_t)N * BK * 2;
         off_a32 = 0;
-        off_buf = kStagesA * a32_bytes;
-        buf_bytes = NS * abf_bytes + NS * b_bytes;
-        off_bar = off_buf + kBufs * buf_bytes;
+        off_buf = Ring<AT>::stages * a32_bytes;
+        buf_bytes = (AT ? 0u : NS * abf_bytes) + NS * b_bytes;
+        off_bar = off_buf + Ring<AT>::bufs * buf_bytes;
         total = off_bar + 256;
     }
 };
@@ -84,6 +94,13 @@ struct TcArgs {
     int chunk_st;                 // K stages per TMEM accumulation chain
     const int *skip;              // optional: the launch does nothing when *skip == 0
     const float *bias;            // optional (A X only): out = A X - 1 bias (implicit centring)
+    // A X only: row tiles >= full_tiles (the last, partial wave of a persistent grid)
+    // are split along K into pieces of tail_per rows, written to tail_part (piece s
+    // at s * tail_stride, rows from full_tiles * 128) and summed by tail_sum_kernel
+    int full_tiles = 0x7fffffff;
+    int64_t tail_per = 0;
+    int64_t tail_stride = 0;
+    float *tail_part = nullptr;
 };
 
 constexpr int kThreads = 512;     // 16 warps
@@ -92,20 +109,24 @@ constexpr int kEpiWarp0 = 4;      // warps 4..7
 
 // ADJ = false: out[128 rows of A] = A X.  ADJ = true: out[128 columns of A] = A^T Q
 // over the rows of one split (GRAM: Q = A, N <= 128).  Persistent: CTA b takes
-// tiles b, b + gridDim.x, ...
-template <int BK, bool ADJ, int NS, bool GRAM>
+// tiles b, b + gridDim.x, ...  AT: the converters write the pieces of A to tensor
+// memory (tcgen05.st; two warps per lane quarter, one K half each) and the MMAs read
+// A from there (N <= 128, so that two accumulators and the A buffers fit 512 columns).
+template <int BK, bool ADJ, int NS, bool GRAM, bool AT = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs args) {
     static_assert(NS == 2 || NS == 3, "two or three BF16 pieces");
     static_assert(!GRAM || ADJ, "the Gram form is an adjoint product");
+    static_assert(!AT || (NS == 2 && !GRAM && BK == 64 && kConvWarps == 8), "tensor-memory A: the split passes");
+    constexpr int kSA = Ring<AT>::stages, kNB = Ring<AT>::bufs;
     if (args.skip && *args.skip == 0) return;                  // uniform: before any setup
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const Plan<BK, NS, GRAM> P(args.N);
+    const Plan<BK, NS, GRAM, AT> P(args.N);
     uint64_t *full_a = reinterpret_cast<uint64_t *>(smem + P.off_bar);
-    uint64_t *empty_a = full_a + kStagesA;
-    uint64_t *full_c = empty_a + kStagesA;
-    uint64_t *empty_c = full_c + kBufs;
-    uint64_t *tm_full = empty_c + kBufs;
+    uint64_t *empty_a = full_a + kSA;
+    uint64_t *full_c = empty_a + kSA;
+    uint64_t *empty_c = full_c + kNB;
+    uint64_t *tm_full = empty_c + kNB;
     uint64_t *tm_empty = tm_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tm_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -113,11 +134,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = args.N;
     const uint32_t acc_cols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-    const uint32_t tmem_cols = 2 * acc_cols;                  // two accumulators
+    // two accumulators (AT: then the kNB x NS pieces of A, 32 columns each)
+    const uint32_t tmem_cols = AT ? 512u : 2 * acc_cols;
+    const uint32_t a_col0 = 2 * acc_cols;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStagesA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
-        for (int b = 0; b < kBufs; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM ? 0 : 1)); mbar_init(&empty_c[b], 1); }
+        for (int s = 0; s < kSA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
+        for (int b = 0; b < kNB; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM ? 0 : 1)); mbar_init(&empty_c[b], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tm_full[a], 1); mbar_init(&tm_empty[a], 4); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -142,12 +165,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         }
         ok = false;
     };
-    // tile -> (first output row, K range)
-    auto tile_info = [&](int t, int64_t &row0, int64_t &kbeg, int &nst) {
-        const int rt = t % args.row_tiles, sp = t / args.row_tiles;
+    // tile -> (first output row, K range, split)
+    auto tile_info = [&](int t, int64_t &row0, int64_t &kbeg, int &nst, int &sp) {
+        int rt;
+        int64_t span;
+        if (!ADJ && t >= args.full_tiles) {
+            const int tails = args.row_tiles - args.full_tiles, u = t - args.full_tiles;
+            rt = args.full_tiles + u % tails;
+            sp = u / tails;
+            kbeg = (int64_t)sp * args.tail_per;
+            span = args.tail_per;
+        } else {
+            rt = t % args.row_tiles;
+            sp = t / args.row_tiles;
+            kbeg = ADJ ? (int64_t)sp * args.per_split : 0;
+            span = ADJ ? args.per_split : args.K;
+        }
         row0 = (int64_t)rt * kBM;
-        kbeg = ADJ ? (int64_t)sp * args.per_split : 0;
-        const int64_t kend = ADJ ? min(args.K, kbeg + args.per_split) : args.K;
+        const int64_t kend = min(args.K, kbeg + span);
         nst = kend > kbeg ? (int)((kend - kbeg + BK - 1) / BK) : 0;
     };
 
@@ -157,11 +192,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             uint32_t g = 0;
             for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
                 int64_t row0, kbeg;
-                int nst;
-                tile_info(t, row0, kbeg, nst);
+                int nst, tsp;
+                tile_info(t, row0, kbeg, nst, tsp);
                 for (int k = 0; k < nst && ok; ++k, ++g) {
-                    const int s = g % kStagesA;
-                    if (g >= kStagesA && !mbar_wait(&empty_a[s], ((g / kStagesA) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    const int s = g % kSA;
+                    if (g >= kSA && !mbar_wait(&empty_a[s], ((g / kSA) & 1) ^ 1, abort_flag)) { fail(); break; }
                     uint8_t *dst = smem + P.off_a32 + s * P.a32_bytes;
                     mbar_arrive_tx(&full_a[s], P.a32_bytes);
                     const int64_t kk = kbeg + (int64_t)k * BK;
@@ -181,16 +216,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             uint32_t g = 0;
             for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
                 int64_t row0, kbeg;
-                int nst;
-                tile_info(t, row0, kbeg, nst);
+                int nst, tsp;
+                tile_info(t, row0, kbeg, nst, tsp);
                 const int64_t stage0 = kbeg / BK;
                 for (int k = 0; k < nst && ok; ++k, ++g) {
-                    const int b = g % kBufs;
-                    if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    const int b = g % kNB;
+                    if (g >= kNB && !mbar_wait(&empty_c[b], ((g / kNB) & 1) ^ 1, abort_flag)) { fail(); break; }
                     uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
                     const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * NS * N * BK;
                     mbar_arrive_tx(&full_c[b], NS * P.b_bytes);
-                    bulk_load(buf + NS * P.abf_bytes, src, NS * P.b_bytes, &full_c[b]);
+                    bulk_load(buf + (AT ? 0u : NS * P.abf_bytes), src, NS * P.b_bytes, &full_c[b]);
                 }
             }
         }
@@ -202,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             uint32_t g = 0, i = 0;
             for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
                 int64_t row0, kbeg;
-                int nst;
-                tile_info(t, row0, kbeg, nst);
+                int nst, tsp;
+                tile_info(t, row0, kbeg, nst, tsp);
                 const int nch = nst > 0 ? (nst + args.chunk_st - 1) / args.chunk_st : 1;
                 int k = 0;
                 for (int ch = 0; ch < nch && ok; ++ch, ++i) {
@@ -213,14 +248,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 const uint32_t d = tmem_base + acc * acc_cols;
                 const int kend = min(nst, k + args.chunk_st);
                 for (int kc = 0; k < kend && ok; ++k, ++kc, ++g) {
-                    const int b = g % kBufs;
-                    if (!mbar_wait(&full_c[b], (g / kBufs) & 1, abort_flag)) { fail(); break; }
+                    const int b = g % kNB;
+                    if (!mbar_wait(&full_c[b], (g / kNB) & 1, abort_flag)) { fail(); break; }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
-                    // piece p of A at base + p * abf_bytes; of B after the NS pieces of A
-                    // (GRAM: B = A)
-                    const uint32_t bbase = GRAM ? base : base + NS * P.abf_bytes;
+                    // piece p of A at base + p * abf_bytes (AT: tensor-memory columns
+                    // a_col0 + (b NS + p) 32); of B after the NS pieces of A (GRAM: B = A)
+                    const uint32_t bbase = GRAM ? base : base + (AT ? 0u : NS * P.abf_bytes);
                     const uint32_t bstep = GRAM ? P.abf_bytes : P.b_bytes;
+                    const uint32_t ta = tmem_base + a_col0 + (uint32_t)(b * NS) * 32u;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t o = kk * 256;
@@ -230,8 +266,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                         for (int q = 0; q < (NS == 2 ? 3 : 6); ++q) {
                             const int pi = NS == 2 ? (q == 2 ? 1 : 0) : (q < 3 ? (q == 2 ? 1 : 0) : q - 3);
                             const int pj = NS == 2 ? (q == 1 ? 1 : 0) : (q < 3 ? (q == 1 ? 1 : 0) : 5 - q);
-                            umma_bf16(d, smem_desc(base + pi * P.abf_bytes + o, LBO, SBO),
-                                      smem_desc(bbase + pj * bstep + o, LBO, SBO), idesc, q == 0 ? acc0 : 1u);
+                            if (AT)
+                                umma_bf16_ts(d, ta + (uint32_t)pi * 32u + (uint32_t)kk * 8u,
+                                             smem_desc(bbase + pj * bstep + o, LBO, SBO), idesc, q == 0 ? acc0 : 1u);
+                            else
+                                umma_bf16(d, smem_desc(base + pi * P.abf_bytes + o, LBO, SBO),
+                                          smem_desc(bbase + pj * bstep + o, LBO, SBO), idesc, q == 0 ? acc0 : 1u);
                         }
                     }
                     umma_commit(&empty_c[b]);
@@ -246,19 +286,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         uint32_t i = 0;
         for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
             int64_t row0, kbeg;
-            int nst;
-            tile_info(t, row0, kbeg, nst);
+            int nst, tsp;
+            tile_info(t, row0, kbeg, nst, tsp);
             const int nch = nst > 0 ? (nst + args.chunk_st - 1) / args.chunk_st : 1;
             for (int ch = 0; ch < nch && ok; ++ch, ++i) {
             const uint32_t acc = i & 1;
             if (!mbar_wait(&tm_full[acc], (i >> 1) & 1, abort_flag)) { fail(); break; }
             tc_fence_after();
-            const int sp = t / args.row_tiles;
+            const bool tail = !ADJ && t >= args.full_tiles;
+            const int sp = tsp;
             const int64_t row = row0 + q * 32 + lane;
-            float *orow = args.out + (int64_t)sp * args.split_stride + row * args.ldo;
+            float *const obase = tail ? args.tail_part : args.out;
+            const int64_t ostride = tail ? args.tail_stride : args.split_stride;
+            float *orow = obase + (int64_t)sp * ostride + (tail ? row - (int64_t)args.full_tiles * kBM : row) * args.ldo;
             const bool live = row < args.out_rows;
-            const bool vec = ((reinterpret_cast<uintptr_t>(args.out) & 15u) == 0) && (args.ldo % 4 == 0) &&
-                             (args.split_stride % 4 == 0);
+            const bool vec = ((reinterpret_cast<uintptr_t>(obase) & 15u) == 0) && (args.ldo % 4 == 0) &&
+                             (ostride % 4 == 0);
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float v[16];
                 if (nst > 0) {
@@ -267,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] = 0.f;
                 }
-                if (!ADJ && args.bias && ch == 0) {
+                if (!ADJ && args.bias && ch == 0 && sp == 0) {
                     // Section 5's implicit centring A*X - ones(m,1)*(c*X), bias = c X
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
@@ -305,14 +348,54 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         uint32_t g = 0;
         for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
             int64_t row0, kbeg;
-            int nst;
-            tile_info(t, row0, kbeg, nst);
+            int nst, tsp;
+            tile_info(t, row0, kbeg, nst, tsp);
             for (int k = 0; k < nst && ok; ++k, ++g) {
-                const int s = g % kStagesA, b = g % kBufs;
-                if (!mbar_wait(&full_a[s], (g / kStagesA) & 1, abort_flag)) { fail(); break; }
-                if (g >= kBufs && !mbar_wait(&empty_c[b], ((g / kBufs) & 1) ^ 1, abort_flag)) { fail(); break; }
+                const int s = g % kSA, b = g % kNB;
+                if (!mbar_wait(&full_a[s], (g / kSA) & 1, abort_flag)) { fail(); break; }
+                if (g >= kNB && !mbar_wait(&empty_c[b], ((g / kNB) & 1) ^ 1, abort_flag)) { fail(); break; }
                 const uint8_t *src = smem + P.off_a32 + s * P.a32_bytes;
                 uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
+                if constexpr (AT) {
+                    // one row of the MMA's A (a row of A for A X, a column of A for A^T Q)
+                    // per thread, the 32 K values of this warp's half of the stage
+                    tc_fence_after();
+                    const int qd = warp & 3, h = (warp - (16 - kConvWarps)) >> 2;
+                    float x[32];
+                    if (!ADJ) {
+                        const int r = qd * 32 + lane;
+                        const uint8_t *row = src + h * (kBM * 128) + r * 128;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float4 v = *reinterpret_cast<const float4 *>(row + ((c ^ (r & 7)) << 4));
+                            x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+                        }
+                    } else {
+                        const uint8_t *box = src + qd * (BK * 128);
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int ii = h * 32 + e;
+                            x[e] = *reinterpret_cast<const float *>(box + ii * 128 + (((lane >> 2) ^ (ii & 7)) << 4) +
+                                                                     (lane & 3) * 4);
+                        }
+                    }
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const __nv_bfloat162 hb = __float22bfloat162_rn(make_float2(x[2 * e], x[2 * e + 1]));
+                        const float2 hf = __bfloat1622float2(hb);
+                        const __nv_bfloat162 lb =
+                            __float22bfloat162_rn(make_float2(x[2 * e] - hf.x, x[2 * e + 1] - hf.y));
+                        hi[e] = bf2_bits(hb);
+                        lo[e] = bf2_bits(lb);
+                    }
+                    const uint32_t ta = tmem_base + ((uint32_t)(qd * 32) << 16) + a_col0 + (uint32_t)(b * NS) * 32u +
+                                        (uint32_t)h * 16u;
+                    tmem_st16(ta, hi);
+                    tmem_st16(ta + 32u, lo);
+                    tmem_st_wait();
+                    tc_fence_before();
+                } else {
                 // core matrices 16 (M) x BK/8 (K); 8 threads per core matrix (one row each)
                 constexpr int tasks = (kBM / 8) * (BK / 8) * 8;
 #pragma unroll
@@ -358,6 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                         *reinterpret_cast<uint4 *>(buf + P.abf_bytes + off) = mid;
                         *reinterpret_cast<uint4 *>(buf + 2 * P.abf_bytes + off) = lo;
                     }
+                }
                 }
                 fence_async_smem();
                 __syncwarp();
@@ -427,6 +511,21 @@ split_block_kernel(const float *__restrict__ P, int64_t rows, int ncols, int64_t
     }
 }
 
+// Y[rows] = sum over the K pieces of the split tail tiles, in piece order (deterministic).
+__global__ void __launch_bounds__(256)
+tail_sum_kernel(const float *__restrict__ part, int pieces, int64_t stride, int64_t rows, int ncols, int64_t ldo,
+                float *__restrict__ Y) {
+    const int64_t total = rows * ncols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / ncols;
+        const int c = (int)(e - r * ncols);
+        const int64_t o = r * ldo + c;
+        float v = part[o];
+        for (int p = 1; p < pieces; ++p) v += part[(int64_t)p * stride + o];
+        Y[o] = v;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -453,11 +552,11 @@ int make_map(CUtensorMap *map, const float *A, int64_t m, int64_t n, int64_t lda
     return r == CUDA_SUCCESS ? RPCA_OK : RPCA_ERR_CUDA;
 }
 
-template <int BK, bool ADJ, int NS = 2, bool GRAM = false>
+template <int BK, bool ADJ, int NS = 2, bool GRAM = false, bool AT = false>
 int launch_pass(const CUtensorMap &map, const TcArgs &a, dim3 grid, cudaStream_t s) {
-    const Plan<BK, NS, GRAM> P(a.N);
+    const Plan<BK, NS, GRAM, AT> P(a.N);
     const size_t smem = P.total + 1024;
-    auto kern = tc_pass_kernel<BK, ADJ, NS, GRAM>;
+    auto kern = tc_pass_kernel<BK, ADJ, NS, GRAM, AT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RPCA_ERR_CUDA;
     kern<<<grid, kThreads, smem, s>>>(map, a);
@@ -511,15 +610,45 @@ int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cu
     return RPCA_OK;
 }
 
+size_t tc_apply_tail_bytes(int lp) { return (size_t)std::max(num_sms(), 1) * kBM * lp * sizeof(float); }
+
 int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *xsplit, int lp,
-                    float *Y, DevStatus *st, cudaStream_t s, const float *bias) {
+                    float *Y, DevStatus *st, cudaStream_t s, const float *bias, float *tail_part) {
     const int N = tc_n(lp), BK = tc_bk(lp);
     CUtensorMap map;
     RPCA_TRY(make_map(&map, A, m, n, lda, 32, kBM));
     const int tiles = (int)cdiv(m, kBM);
     TcArgs a{xsplit, Y, m, lp, lp, N, n, n, 0, tiles, tiles, st, std::max(1, kChunkRows / BK), nullptr, bias};
-    dim3 grid((unsigned)std::min(tiles, num_sms()), 1, 1);
-    return BK == 64 ? launch_pass<64, false>(map, a, grid, s) : launch_pass<32, false>(map, a, grid, s);
+    // The persistent grid takes the tiles in waves of one per SM.  When the last wave
+    // is partial (R tiles), its tiles are split along K into S <= SMs / R pieces of at
+    // least four stages, so that the wave takes about 1/S of a tile's time.
+    const int sms = num_sms();
+    const int R = tiles % sms;
+    int pieces = 1;
+    if (tail_part && R > 0) {
+        const int64_t stages = cdiv(n, BK);
+        const int64_t want = std::min<int64_t>(sms / R, stages / 4);
+        if (want >= 2) {
+            a.tail_per = round_up(cdiv(n, want), BK);
+            pieces = (int)cdiv(n, a.tail_per);
+        }
+    }
+    if (pieces >= 2) {
+        a.full_tiles = tiles - R;
+        a.tail_stride = (int64_t)R * kBM * lp;
+        a.tail_part = tail_part;
+        a.ntiles = a.full_tiles + R * pieces;
+    }
+    dim3 grid((unsigned)std::min(a.ntiles, sms), 1, 1);
+    // N <= 128 (BK = 64): A in tensor memory
+    RPCA_TRY(BK == 64 ? (launch_pass<64, false, 2, false, true>(map, a, grid, s)) : (launch_pass<32, false>(map, a, grid, s)));
+    if (pieces >= 2) {
+        const int64_t r0 = (int64_t)a.full_tiles * kBM, rows = m - r0;
+        const int64_t g = std::max<int64_t>(1, std::min<int64_t>(cdiv(rows * lp, 256), (int64_t)sms * 4));
+        tail_sum_kernel<<<(unsigned)g, 256, 0, s>>>(tail_part, pieces, a.tail_stride, rows, lp, lp, Y + r0 * lp);
+        RPCA_CHECK_LAUNCH();
+    }
+    return RPCA_OK;
 }
 
 int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *qsplit, int lp,
@@ -532,7 +661,7 @@ int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const _
     TcArgs a{qsplit, part, n, lp, lp, N, per, m, n * (int64_t)lp, rt, rt * splits, st, std::max(1, kChunkRows / BK),
              nullptr};
     dim3 grid((unsigned)std::min(rt * splits, num_sms()), 1, 1);
-    return BK == 64 ? launch_pass<64, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
+    return BK == 64 ? launch_pass<64, true, 2, false, true>(map, a, grid, s) : launch_pass<32, true>(map, a, grid, s);
 }
 
 // ---------------------------------------------------------------------------

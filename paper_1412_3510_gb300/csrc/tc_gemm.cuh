@@ -16,8 +16,12 @@ int tc_adjoint_splits(int64_t n, int64_t m, int lp);
 // FP32 block P (rows x lp) -> BF16 hi/lo per stage in the MMA's K-major layout.
 int launch_tc_split(const float *P, int64_t rows, int lp, __nv_bfloat16 *out, cudaStream_t s);
 // Y (m x lp) = A X, X given pre-split; with bias (lp values), Y = A X - 1 bias.
+// tail_part (optional, tc_apply_tail_bytes(lp) bytes): room for the K pieces of the
+// last partial wave of row tiles; without it that wave runs unsplit.
+size_t tc_apply_tail_bytes(int lp);
 int launch_tc_apply(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *xsplit, int lp,
-                    float *Y, DevStatus *st, cudaStream_t s, const float *bias = nullptr);
+                    float *Y, DevStatus *st, cudaStream_t s, const float *bias = nullptr,
+                    float *tail_part = nullptr);
 // part[s] (n x lp) = A^T Q over the rows of split s, Q given pre-split.
 int launch_tc_adjoint(const float *A, int64_t m, int64_t n, int64_t lda, const __nv_bfloat16 *qsplit, int lp,
                       float *part, int splits, DevStatus *st, cudaStream_t s);

@@ -20,13 +20,16 @@ Bars (readings of "sigma within 1e-4 relative, residual within 1e-3 relative"):
   oracle's, both from the Section 4 estimator (60 iterations, same start vector)
   and exactly (FP64 Gram of the residual).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
 import oracle as O
 import synth as S
-from gpu_util import cuda, exact_resid_device, subspace_dist, to_dev, to_np
+from gpu_util import cuda, exact_resid_device, exact_singular_values_device, subspace_dist, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 SEED = 1
@@ -41,7 +44,18 @@ def _sigma_bar(sg, so):
     assert np.all(np.abs(sg - so) <= 1e-4 * so + 2e-6 * so[0]), rel.max()
 
 
-def _parity(Ad, Ah, k, l, its, raw, precision, oracle_out):
+_SK1 = {}
+
+
+def _report(record):
+    """Append one JSON line of measured figures when RPCA_PARITY_REPORT names a file."""
+    path = os.environ.get("RPCA_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(record) + "\n")
+
+
+def _parity(Ad, Ah, k, l, its, raw, precision, oracle_out, key=None):
     import paper_1412_3510_gb300 as rp
     m, n = Ah.shape
     opts = rp.make_opts(k, l, its, raw, seed=SEED, precision=precision)
@@ -56,6 +70,20 @@ def _parity(Ad, Ah, k, l, its, raw, precision, oracle_out):
     assert abs(est - est_o) <= 1e-3 * est_o, (est, est_o)
     exact = exact_resid_device(Ad, U, Sg, V, raw)
     assert abs(exact - exact_o) <= 1e-3 * exact_o, (exact, exact_o)
+    if key is not None and os.environ.get("RPCA_PARITY_REPORT"):
+        if key not in _SK1:
+            _SK1[key] = float(exact_singular_values_device(Ad, raw)[k])
+        sg = to_np(Sg)
+        half = len(so) // 2
+        rel = np.abs(sg - so) / so
+        _report({"matrix": key, "shape": [m, n], "k": k, "l": l, "its": its, "raw": raw,
+                 "precision": precision, "exact_gpu": exact, "exact_oracle": exact_o,
+                 "sigma_k1": _SK1[key], "exact_gpu_over_sigma_k1": exact / _SK1[key],
+                 "exact_oracle_over_sigma_k1": exact_o / _SK1[key],
+                 "est60_gpu": est, "est60_oracle": est_o,
+                 "sigma_rel_max_lead_half": float(rel[:half].max()),
+                 "sigma_abs_max_tail_over_s1": float(np.abs(sg - so)[half:].max() / so[0]),
+                 "shifts": int(block["shifts"])})
     # the estimator never exceeds the norm and has converged at 60 iterations
     assert est <= exact * (1 + 1e-5) and est >= exact * (1 - 1e-3)
     return block
@@ -95,7 +123,8 @@ def test_benchmark_matrix_parity(its, precision):
     """The benchmark's 100000 x 2000 matrix: same A, same Omega as the oracle."""
     cuda()
     Ad, Ah = _benchmark_matrix()
-    block = _parity(Ad, Ah, 100, 102, its, False, precision, _oracle("bench", Ad, Ah, 100, 102, its, False))
+    block = _parity(Ad, Ah, 100, 102, its, False, precision,
+                    _oracle("bench", Ad, Ah, 100, 102, its, False), key="dense_100000x2000_k100")
     # one shifted Cholesky at most per PCA on this spectrum (the first round of the final
     # orthonormalisation, whose block has condition ~ sigma_1 / sigma_102 = 1e3)
     assert block["shifts"] <= 1 and block["status"] in (0, 1)
@@ -109,7 +138,8 @@ def test_graded_spectrum_parity(precision):
         Ah = S.haar_dense_np(20000, 2000, S.spectrum_pow15(2000, 77), seed=78)
         _MATS["graded"] = (to_dev(Ah), Ah)
     Ad, Ah = _MATS["graded"]
-    block = _parity(Ad, Ah, 100, 102, 2, False, precision, _oracle("graded", Ad, Ah, 100, 102, 2, False))
+    block = _parity(Ad, Ah, 100, 102, 2, False, precision,
+                    _oracle("graded", Ad, Ah, 100, 102, 2, False), key="graded_20000x2000_k100")
     assert block["shifts"] <= 1
 
 

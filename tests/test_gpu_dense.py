@@ -101,13 +101,18 @@ def test_exact_low_rank_recovery_tall(raw):
     A = (rng.standard_normal((20000, r)) @ rng.standard_normal((r, 300))).astype(np.float32)
     if not raw:
         A += np.float32(2.0)
+    # Bars: the Gram of the 20000-row block runs on the tensor cores, whose FP32
+    # accumulation drifts by up to ~2e-6 relative (256-row chains), so Q and U = Q W are
+    # orthonormal to a few 1e-6 and the reconstruction error is of that order
+    # (measured 1.2e-6 .. 2.5e-6 in both pass precisions; 4e-6 = 67 u_32).
     for l in (11, 9):
         U, Sg, V = rp.rpca_dense(to_dev(A), 9, l, its=1, raw=raw, seed=4)
         Ac = A.astype(np.float64) - (0 if raw else A.astype(np.float64).mean(0))
         E = Ac - (to_np(U) * to_np(Sg)) @ to_np(V).T
-        assert np.linalg.norm(E, 2) / np.linalg.norm(Ac, 2) < 2e-6, l
-        Ug = to_np(U)
-        assert np.linalg.norm(Ug.T @ Ug - np.eye(9), 2) < 1e-4
+        assert np.linalg.norm(E, 2) / np.linalg.norm(Ac, 2) < 4e-6, l
+        Ug, Vg = to_np(U), to_np(V)
+        assert np.linalg.norm(Ug.T @ Ug - np.eye(9), 2) < 1e-5
+        assert np.linalg.norm(Vg.T @ Vg - np.eye(9), 2) < 1e-5
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
