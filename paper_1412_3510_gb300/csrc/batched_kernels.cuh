@@ -478,12 +478,19 @@ __device__ void small_svd(Smem &sm, int l) {
         __syncthreads();
         if (!rot) break;
     }
-    // sigma_j = |M_j|; rank descending (ties by index)
+    // sigma_j = |M_j| / |Z_j|: the rotations are orthogonal only to a few ulps with a
+    // systematic sign and scale M_j and Z_j alike, so the ratio and Z_j / |Z_j| remove
+    // that drift; rank descending (ties by index).  sm.sig holds 1 / |Z_j| meanwhile.
     if (threadIdx.x < l) {
         const int j = threadIdx.x;
-        float s2 = 0.f;
-        for (int i = 0; i < l; ++i) s2 = fmaf(M[j * l + i], M[j * l + i], s2);
-        sm.vec[j] = sqrtf(s2);
+        float s2 = 0.f, z2 = 0.f;
+        for (int i = 0; i < l; ++i) {
+            s2 = fmaf(M[j * l + i], M[j * l + i], s2);
+            z2 = fmaf(Z[j * l + i], Z[j * l + i], z2);
+        }
+        const float iz = z2 > 0.f ? 1.f / sqrtf(z2) : 1.f;
+        sm.vec[j] = sqrtf(s2) * iz;
+        sm.sig[j] = iz;
     }
     __syncthreads();
     if (threadIdx.x < l) {
@@ -492,17 +499,19 @@ __device__ void small_svd(Smem &sm, int l) {
         int rank = 0;
         for (int i = 0; i < l; ++i) rank += (sm.vec[i] > sj) || (sm.vec[i] == sj && i < j);
         sm.perm[rank] = j;
-        sm.sig[rank] = sj;
     }
     __syncthreads();
-    // W[:, r] = M_{perm[r]} / sigma_r (stored as G[i * l + r]);  Zs[:, r] = Z_{perm[r]} (stored in Racc)
+    // W[:, r] = M_{perm[r]} / |M_{perm[r]}| (stored as G[i * l + r]);  Zs[:, r] = Z_{perm[r]} / |Z_{perm[r]}|
+    // (stored in Racc)
     for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
         const int i = e / l, r = e % l;
         const int j = sm.perm[r];
-        const float s = sm.vec[j];
-        sm.G[i * l + r] = s > 0.f ? M[j * l + i] / s : 0.f;
-        sm.Racc[i * l + r] = Z[j * l + i];
+        const float s = sm.vec[j], iz = sm.sig[j];
+        sm.G[i * l + r] = s > 0.f ? M[j * l + i] * iz / s : 0.f;
+        sm.Racc[i * l + r] = Z[j * l + i] * iz;
     }
+    __syncthreads();
+    if (threadIdx.x < l) sm.sig[threadIdx.x] = sm.vec[sm.perm[threadIdx.x]];
     __syncthreads();
 }
 

@@ -49,14 +49,17 @@ constexpr int kBM = 128;              // MMA M and CTA output rows
 constexpr int kChunkRows = 2048;
 constexpr int kStagesA = 3;           // FP32 A ring depth
 constexpr int kBufs = 2;              // converted BF16 buffers
-// A in tensor memory (AT): the converted pieces of A leave shared memory, which then
-// holds a deeper FP32 ring (more bytes of A in flight per SM)
-constexpr int kStagesAT = 5;
-constexpr int kBufsAT = 2;
+// A in tensor memory (AT): the converted pieces of A leave shared memory, and the
+// block operand gets a ring of its own, so that its copies (from L2) run ahead of
+// the MMAs instead of waiting for the buffer the converted A shares with them
+constexpr int kStagesAT = 3;          // FP32 A ring
+constexpr int kBufsAT = 4;            // converted A buffers in tensor memory (with two N <= 128 accumulators: 512 columns)
+constexpr int kBBufsAT = 4;           // block-operand ring
 template <bool AT>
 struct Ring {
     static constexpr int stages = AT ? kStagesAT : kStagesA;
     static constexpr int bufs = AT ? kBufsAT : kBufs;
+    static constexpr int bbufs = AT ? kBBufsAT : kBufs;   // without AT: the converted buffers
 };
 
 // Shared-memory plan of one CTA (byte offsets from a 1024-aligned base).  NS BF16
@@ -73,7 +76,7 @@ struct Plan {
         off_a32 = 0;
         off_buf = Ring<AT>::stages * a32_bytes;
         buf_bytes = (AT ? 0u : NS * abf_bytes) + NS * b_bytes;
-        off_bar = off_buf + Ring<AT>::bufs * buf_bytes;
+        off_bar = off_buf + Ring<AT>::bbufs * buf_bytes;
         total = off_bar + 256;
     }
 };
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     static_assert(NS == 2 || NS == 3, "two or three BF16 pieces");
     static_assert(!GRAM || ADJ, "the Gram form is an adjoint product");
     static_assert(!AT || (NS == 2 && !GRAM && BK == 64 && kConvWarps == 8), "tensor-memory A: the split passes");
-    constexpr int kSA = Ring<AT>::stages, kNB = Ring<AT>::bufs;
+    constexpr int kSA = Ring<AT>::stages, kNB = Ring<AT>::bufs, kNBB = Ring<AT>::bbufs;
     if (args.skip && *args.skip == 0) return;                  // uniform: before any setup
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -126,7 +129,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     uint64_t *empty_a = full_a + kSA;
     uint64_t *full_c = empty_a + kSA;
     uint64_t *empty_c = full_c + kNB;
-    uint64_t *tm_full = empty_c + kNB;
+    uint64_t *full_b = empty_c + kNB;             // AT: the block-operand ring
+    uint64_t *empty_b = full_b + kNBB;
+    uint64_t *tm_full = empty_b + kNBB;
     uint64_t *tm_empty = tm_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tm_empty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -140,7 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSA; ++s) { mbar_init(&full_a[s], 1); mbar_init(&empty_a[s], kConvWarps); }
-        for (int b = 0; b < kNB; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM ? 0 : 1)); mbar_init(&empty_c[b], 1); }
+        for (int b = 0; b < kNB; ++b) { mbar_init(&full_c[b], kConvWarps + (GRAM || AT ? 0 : 1)); mbar_init(&empty_c[b], 1); }
+        for (int b = 0; b < kNBB; ++b) { mbar_init(&full_b[b], 1); mbar_init(&empty_b[b], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tm_full[a], 1); mbar_init(&tm_empty[a], 4); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,12 +226,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 tile_info(t, row0, kbeg, nst, tsp);
                 const int64_t stage0 = kbeg / BK;
                 for (int k = 0; k < nst && ok; ++k, ++g) {
-                    const int b = g % kNB;
-                    if (g >= kNB && !mbar_wait(&empty_c[b], ((g / kNB) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    const int b = g % kNBB;
+                    uint64_t *fb = AT ? &full_b[b] : &full_c[b];
+                    uint64_t *eb = AT ? &empty_b[b] : &empty_c[b];
+                    if (g >= kNBB && !mbar_wait(eb, ((g / kNBB) & 1) ^ 1, abort_flag)) { fail(); break; }
                     uint8_t *buf = smem + P.off_buf + b * P.buf_bytes;
                     const __nv_bfloat16 *src = args.bsplit + (size_t)(stage0 + k) * NS * N * BK;
-                    mbar_arrive_tx(&full_c[b], NS * P.b_bytes);
-                    bulk_load(buf + (AT ? 0u : NS * P.abf_bytes), src, NS * P.b_bytes, &full_c[b]);
+                    mbar_arrive_tx(fb, NS * P.b_bytes);
+                    bulk_load(buf + (AT ? 0u : NS * P.abf_bytes), src, NS * P.b_bytes, fb);
                 }
             }
         }
@@ -248,10 +256,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                 const uint32_t d = tmem_base + acc * acc_cols;
                 const int kend = min(nst, k + args.chunk_st);
                 for (int kc = 0; k < kend && ok; ++k, ++kc, ++g) {
-                    const int b = g % kNB;
+                    const int b = g % kNB, bb = AT ? (int)(g % kNBB) : b;
                     if (!mbar_wait(&full_c[b], (g / kNB) & 1, abort_flag)) { fail(); break; }
+                    if (AT && !mbar_wait(&full_b[bb], (g / kNBB) & 1, abort_flag)) { fail(); break; }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + P.off_buf + b * P.buf_bytes);
+                    const uint32_t base = smem_u32(smem + P.off_buf + bb * P.buf_bytes);
                     // piece p of A at base + p * abf_bytes (AT: tensor-memory columns
                     // a_col0 + (b NS + p) 32); of B after the NS pieces of A (GRAM: B = A)
                     const uint32_t bbase = GRAM ? base : base + (AT ? 0u : NS * P.abf_bytes);
@@ -275,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
                         }
                     }
                     umma_commit(&empty_c[b]);
+                    if (AT) umma_commit(&empty_b[bb]);
                 }
                 if (ok) umma_commit(&tm_full[acc]);
                 }
