@@ -185,18 +185,6 @@ radix_scatter_kernel(const int32_t *__restrict__ kin, const int32_t *__restrict_
 }
 
 // colptr[c] = first position whose key >= c (c = 0..n)
-// Sort keys of the column-blocked transpose: key = (row / chunk_rows) * n + column, so
-// that the stable sort yields one CSR of A^T per block of chunk_rows rows of A (the
-// block operand's rows that block gathers stay resident in L2).  Out-of-range
-// columns (reported by csr_check_kernel) are clamped so that every key is in range.
-__global__ void blocked_key_kernel(const int32_t *__restrict__ row_of, const int32_t *__restrict__ col,
-                                   int64_t nnz, int64_t chunk_rows, int64_t n, int32_t *__restrict__ keys) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = min(max((int64_t)col[p], (int64_t)0), n - 1);
-        keys[p] = (int32_t)(((int64_t)row_of[p] / chunk_rows) * n + j);
-    }
-}
-
 __global__ void colptr_kernel(const int32_t *__restrict__ keys, int64_t nnz, int64_t n, int32_t *__restrict__ colptr) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= n; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = nnz;
@@ -285,21 +273,20 @@ __device__ __forceinline__ void row_dot(const int32_t *__restrict__ idx, const f
 // light rows: Y[r] = sum_p val[p] X[idx[p]] (heavy rows are skipped)
 __global__ void __launch_bounds__(256)
 spmm_light_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, const float *__restrict__ val,
-                  int64_t rows, int64_t cols, int64_t nnz, const float *__restrict__ X, int lp, float *__restrict__ Y,
-                  bool add) {
+                  int64_t rows, int64_t cols, int64_t nnz, const float *__restrict__ X, int lp, float *__restrict__ Y) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = wid; r < rows; r += nw) {
         const int32_t p0 = max(ptr[r], 0), p1 = min((int64_t)ptr[r + 1], nnz);
-        if (p1 - p0 > kHeavy || (add && p1 <= p0)) continue;
+        if (p1 - p0 > kHeavy) continue;
         for (int c0 = 0; c0 < lp; c0 += 128) {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             row_dot(idx, val, p0, p1, cols, X, lp, c0, lane, acc);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = lane + 32 * q;
-                if (c0 + c < lp) Y[r * lp + c0 + c] = add ? Y[r * lp + c0 + c] + acc[q] : acc[q];
+                if (c0 + c < lp) Y[r * lp + c0 + c] = acc[q];
             }
         }
     }
@@ -355,12 +342,12 @@ __device__ __forceinline__ void group_dot(const int32_t *__restrict__ idx, const
 
 // light rows with several rows per warp: a group of G lanes per row, every warp keeping
 // (32 / G) x 4 x 2 float4 gathers in flight.  Needs lp % 4 == 0 and lp <= 8 G; heavy
-// rows are skipped.  add: Y[r] += the row's sum (rows without nonzeros untouched).
+// rows are skipped.
 template <int G>
 __global__ void __launch_bounds__(256, 4)
 spmm_light_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                         const float *__restrict__ val, int64_t rows, int64_t cols, int64_t nnz,
-                        const float *__restrict__ X, int lp, float *__restrict__ Y, bool add) {
+                        const float *__restrict__ X, int lp, float *__restrict__ Y) {
     constexpr int R = 32 / G;                  // rows per warp
     const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -375,17 +362,13 @@ spmm_light_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restri
         if (r < rows) {
             p0 = max(ptr[r], 0);
             p1 = (int32_t)min((int64_t)ptr[r + 1], nnz);
-            write = p1 - p0 <= kHeavy && !(add && p1 <= p0);
+            write = p1 - p0 <= kHeavy;
             if (!write) p1 = p0;
         }
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
         group_dot<G>(idx, val, p0, p1, cols, X4, nv, sub, c0ok, c1ok, a0, a1);
         if (write) {
             float4 *yr = reinterpret_cast<float4 *>(Y) + r * nv;
-            if (add) {
-                if (c0ok) { const float4 y = yr[sub]; a0.x += y.x; a0.y += y.y; a0.z += y.z; a0.w += y.w; }
-                if (c1ok) { const float4 y = yr[sub + G]; a1.x += y.x; a1.y += y.y; a1.z += y.z; a1.w += y.w; }
-            }
             if (c0ok) yr[sub] = a0;
             if (c1ok) yr[sub + G] = a1;
         }
@@ -455,7 +438,7 @@ spmm_heavy_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ i
 // found through the chunk table (the row's first chunk, q = 0)
 __global__ void __launch_bounds__(256)
 spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, const int2 *__restrict__ table, int64_t rows,
-                         int64_t max_chunks, const float *__restrict__ part, int lp, float *__restrict__ Y, bool add) {
+                         int64_t max_chunks, const float *__restrict__ part, int lp, float *__restrict__ Y) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -468,7 +451,7 @@ spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, const int2 *__restri
         for (int c = lane; c < lp; c += 32) {
             float s = 0.f;
             for (int64_t k = c0; k < c1; ++k) s += part[k * lp + c];
-            Y[r * lp + c] = add ? Y[r * lp + c] + s : s;
+            Y[r * lp + c] = s;
         }
     }
 }
@@ -497,18 +480,17 @@ struct Spmm {
         }
         return RPCA_OK;
     }
-    // add: Y += the product (A^T in column blocks, each block's product added in turn)
-    int run(const float *X, int lp, float *Y, cudaStream_t s, bool add = false) const {
+    int run(const float *X, int lp, float *Y, cudaStream_t s) const {
         const bool vec = lp % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
                          (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
         if (vec && lp <= 64) {
-            spmm_light_group_kernel<8><<<grid_for(rows * 8, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, add);
+            spmm_light_group_kernel<8><<<grid_for(rows * 8, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
         } else if (vec && lp <= 128) {
-            spmm_light_group_kernel<16><<<grid_for(rows * 16, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, add);
+            spmm_light_group_kernel<16><<<grid_for(rows * 16, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
         } else if (vec && lp <= 256) {
-            spmm_light_group_kernel<32><<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, add);
+            spmm_light_group_kernel<32><<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
         } else {
-            spmm_light_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, add);
+            spmm_light_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
         }
         RPCA_CHECK_LAUNCH();
         if (max_chunks > 0) {
@@ -527,7 +509,7 @@ struct Spmm {
             }
             RPCA_CHECK_LAUNCH();
             spmm_heavy_reduce_kernel<<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(first, table, rows, max_chunks,
-                                                                                   part, lp, Y, add);
+                                                                                   part, lp, Y);
             RPCA_CHECK_LAUNCH();
         }
         return RPCA_OK;
@@ -540,28 +522,13 @@ int64_t max_chunks_for(int64_t nnz, int64_t rows) {
     return 2 * (nnz / kHeavy) + 1;
 }
 
-// A^T in column blocks: rows of the block operand per block sized so that a block's
-// rows (lp floats each) take about a third of L2
-constexpr int kMaxTChunks = 8;
-constexpr int64_t kTChunkBytes = 40ll << 20;
-
-int tchunks_for(int64_t m, int64_t n, int lp) {
-    int64_t c = cdiv(m * (int64_t)lp * 4, kTChunkBytes);
-    c = std::min<int64_t>(std::max<int64_t>(c, 1), kMaxTChunks);
-    while (c > 1 && c * n >= INT32_MAX) --c;
-    return (int)c;
-}
-
 struct CsrScratch {
-    int tchunks = 1;
     size_t row_of = 0, keys0 = 0, keys1 = 0, rows0 = 0, rows1 = 0, vals0 = 0, vals1 = 0, hist = 0, tptr = 0,
            first_a = 0, first_t = 0, table_a = 0, table_t = 0, part_a = 0, part_t = 0, scan = 0, total = 0;
 };
 
 CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
     CsrScratch S;
-    S.tchunks = tchunks_for(m, n, max_lp);
-    const int C = S.tchunks;
     size_t off = 0;
     auto take = [&](size_t b) { const size_t o = off; off = (off + b + 255) & ~(size_t)255; return o; };
     const int64_t nblocks = cdiv(std::max<int64_t>(nnz, 1), kTile);
@@ -573,11 +540,11 @@ CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
     S.vals0 = take((size_t)nnz * 4);
     S.vals1 = take((size_t)nnz * 4);
     S.hist = take((size_t)256 * nblocks * 4);
-    S.tptr = take((size_t)(C * n + 1) * 4);
+    S.tptr = take((size_t)(n + 1) * 4);
     S.first_a = take((size_t)(m + 1) * 4);
-    S.first_t = take((size_t)C * (n + 1) * 4);
+    S.first_t = take((size_t)(n + 1) * 4);
     S.table_a = take((size_t)max_chunks_for(nnz, m) * 8);
-    S.table_t = take((size_t)C * max_chunks_for(nnz, n) * 8);
+    S.table_t = take((size_t)max_chunks_for(nnz, n) * 8);
     S.part_a = take((size_t)max_chunks_for(nnz, m) * max_lp * 4);
     S.part_t = take((size_t)max_chunks_for(nnz, n) * max_lp * 4);
     S.scan = take((size_t)scan_tiles(std::max({(int64_t)256 * nblocks, m + 1, n + 1})) * 8);
@@ -587,8 +554,7 @@ CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
 
 // A (CSR) and A^T (CSR, built by the stable sort) as the pipeline's operator.
 struct CsrOp final : Operator {
-    Spmm a, t[kMaxTChunks];       // A; A^T in tchunks column blocks
-    int tchunks = 1;
+    Spmm a, t;
     int apply(const float *X, int lp, float *Y, cudaStream_t s, const float *) const override {
         TimedScope ts(kTimeApplyKernel, s);
         return a.run(X, lp, Y, s);
@@ -596,8 +562,7 @@ struct CsrOp final : Operator {
     int adjoint_splits(int) const override { return 1; }
     int adjoint(const float *Q, int lp, float *part, cudaStream_t s) const override {
         TimedScope ts(kTimeAdjointKernel, s);
-        for (int c = 0; c < tchunks; ++c) RPCA_TRY(t[c].run(Q, lp, part, s, c > 0));
-        return RPCA_OK;
+        return t.run(Q, lp, part, s);
     }
 };
 
@@ -621,16 +586,13 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     if (nnz > 0) {
         nnz_row_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(row_ptr, m, nnz, rws[0]);
         RPCA_CHECK_LAUNCH();
-        if (S.tchunks > 1)
-            blocked_key_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(rws[0], col_idx, nnz, cdiv(m, S.tchunks), n, keys[0]);
-        else
-            copy_i32_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(col_idx, keys[0], nnz);
+        copy_i32_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(col_idx, keys[0], nnz);
         RPCA_CHECK_LAUNCH();
         copy_f32_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(val, vls[0], nnz);
         RPCA_CHECK_LAUNCH();
         const int nblocks = (int)cdiv(nnz, kTile);
         int bits = 1;
-        while (bits < 31 && (1LL << bits) < (int64_t)S.tchunks * n) ++bits;
+        while (bits < 31 && (1LL << bits) < n) ++bits;
         for (int shift = 0; shift < bits; shift += 8) {
             radix_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(keys[cur], nnz, shift, I(S.hist), nblocks);
             RPCA_CHECK_LAUNCH();
@@ -641,25 +603,14 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
             cur ^= 1;
         }
     }
-    const int64_t C = S.tchunks;
-    colptr_kernel<<<grid_for(C * n + 1, 256), 256, 0, s>>>(keys[cur], nnz, C * n, I(S.tptr));
+    colptr_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(keys[cur], nnz, n, I(S.tptr));
     RPCA_CHECK_LAUNCH();
+    op.t.ptr = I(S.tptr); op.t.idx = rws[cur]; op.t.val = vls[cur];
+    op.t.rows = n; op.t.cols = m; op.t.nnz = nnz; op.t.max_chunks = max_chunks_for(nnz, n);
+    op.t.first = I(S.first_t); op.t.table = reinterpret_cast<int2 *>(base + S.table_t); op.t.part = F(S.part_t);
+    op.t.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
     RPCA_TRY(op.a.plan(s));
-    op.tchunks = (int)C;
-    const int64_t mc = max_chunks_for(nnz, n);
-    for (int64_t c = 0; c < C; ++c) {
-        // block c: the CSR of A^T restricted to rows [c chunk_rows, (c + 1) chunk_rows) of A;
-        // its row pointers are the sorted keys' boundaries c n .. c n + n (positions in the
-        // shared index and value arrays); the partial buffer is shared (blocks run in turn)
-        Spmm &t = op.t[c];
-        t.ptr = I(S.tptr) + c * n; t.idx = rws[cur]; t.val = vls[cur];
-        t.rows = n; t.cols = m; t.nnz = nnz; t.max_chunks = mc;
-        t.first = I(S.first_t) + c * (n + 1);
-        t.table = reinterpret_cast<int2 *>(base + S.table_t) + c * mc;
-        t.part = F(S.part_t);
-        t.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
-        RPCA_TRY(t.plan(s));
-    }
+    RPCA_TRY(op.t.plan(s));
     return RPCA_OK;
 }
 

@@ -56,10 +56,9 @@ def test_tall_csr_parity():
     _check(csr, 6, 10, 2, False, seed=3)
 
 
-def test_column_blocked_transpose_parity():
-    """400000 rows, l = 30 (lp = 32): the block operand's rows (51 MB) exceed the 40 MiB
-    block budget, so A^T is built in two column blocks whose products are added in turn;
-    the power-law columns give heavy rows of A^T that straddle the block boundary."""
+def test_tall_powerlaw_csr_parity():
+    """400000 rows, l = 30: heavy rows of A^T (power-law columns) much longer than a chunk,
+    and the m-side block (51 MB) on the tensor-core renormalisations."""
     rp_, ci, va = S.powerlaw_csr(400000, 3000, 2000000, exponent=2.1, rank=8, seed=21)
     csr = sp.csr_matrix((va, ci, rp_), shape=(400000, 3000))
     assert np.diff(csr.tocsc().indptr).max() > 256       # heavy rows of A^T exist
