@@ -253,6 +253,7 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
     __shared__ CholShared cs;
     __shared__ float rdinv[RPCA_MAX_L];           // 1 / R_jj of the factored panels
     __shared__ __align__(16) float Xd[kNB * kXdLd];   // inverse of the current diagonal block
+    __shared__ float thr_s[kNB], rdi_s[kNB];
     __shared__ int s_broke;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -274,18 +275,20 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
             //    inverse X (column c of X in lane c); R goes to the upper triangle, the
             //    strictly upper part of X transposed to the strictly lower triangle
             if (warp == 0) {
+                // Lane c holds column c of the block; the rows of R go through shared memory
+                // for the inverse (broadcast reads instead of a shuffle per entry).
                 const int c = lane;
                 float a[kNB];
 #pragma unroll
                 for (int r = 0; r < kNB; ++r) a[r] = (r <= c && c < bl) ? A[(b0 + r) * ld + b0 + c] : 0.f;
-                const float thr = c < bl ? tau * cs.dorig[b0 + c] + 0.5f * shift : 0.f;
+                thr_s[c] = c < bl ? tau * cs.dorig[b0 + c] + 0.5f * shift : 0.f;
+                __syncwarp();
                 bool fail = false;
                 float rd = 1.f;                             // this lane's R_cc
 #pragma unroll
                 for (int j = 0; j < kNB; ++j) {
                     const float d = __shfl_sync(0xffffffffu, a[j], j);
-                    const float t = __shfl_sync(0xffffffffu, thr, j);
-                    const bool good = j >= bl || (d > t && d > 0.f);
+                    const bool good = j >= bl || (d > thr_s[j] && d > 0.f);
                     fail |= !good;                          // uniform: every lane sees d
                     a[j] *= rsqrtf(j < bl && good ? d : 1.f);   // row j of R: r_jc (lane j: sqrt(d))
                     if (lane == j) rd = a[j];
@@ -302,6 +305,15 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
                     if (lane == 0) s_broke = 1;
                 } else {
                     const float rdi = c < bl ? 1.0f / rd : 0.f;
+                    // row i of R (entries r_it, t > i, held by lane t) to shared memory (Xd holds
+                    // it until X replaces it), and R's upper triangle to A
+#pragma unroll
+                    for (int r = 0; r < kNB; ++r) {
+                        Xd[r * kXdLd + c] = (r < c) ? a[r] : 0.f;
+                        if (c < bl && r < c) A[(b0 + r) * ld + b0 + c] = a[r];
+                    }
+                    rdi_s[c] = rdi;
+                    __syncwarp();
                     // R x = e_c from the bottom: x_i = ([i == c] - sum_{t > i} r_it x_t) / r_ii
                     float x[kNB];
 #pragma unroll
@@ -310,19 +322,17 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
 #pragma unroll
                         for (int t = 0; t < kNB; ++t) {
                             if (t > i) {
-                                const float v = __shfl_sync(0xffffffffu, a[i], t);
+                                const float v = Xd[i * kXdLd + t];
                                 if (t & 1) s1 = fmaf(-v, x[t], s1);
                                 else s0 = fmaf(-v, x[t], s0);
                             }
                         }
-                        x[i] = (s0 + s1) * __shfl_sync(0xffffffffu, rdi, i);
+                        x[i] = (s0 + s1) * rdi_s[i];
                     }
+                    __syncwarp();                           // every lane has read R from Xd
 #pragma unroll
                     for (int r = 0; r < kNB; ++r) {
-                        if (c < bl && r < c) {
-                            A[(b0 + r) * ld + b0 + c] = a[r];
-                            A[(b0 + c) * ld + b0 + r] = x[r];
-                        }
+                        if (c < bl && r < c) A[(b0 + c) * ld + b0 + r] = x[r];
                         Xd[r * kXdLd + c] = (c < bl && r <= c) ? x[r] : 0.f;
                     }
                     if (c < bl) {
