@@ -158,8 +158,9 @@ constexpr int kXdLd = kNB + 4;                    // row stride of the diagonal 
 __host__ __device__ __forceinline__ int chol_ld(int l) { return (l + 3) & ~3; }
 
 // Block rows of X = R^-1 (ld a multiple of 4, diagonal blocks already inverted) in
-// 4 x 4 register tiles; the strictly lower triangle is cleared first so that every
+// 2 x 4 register tiles; the strictly lower triangle is cleared first so that every
 // sum runs over whole tiles.  S: kNB x (ld - kNB) scratch.  Then Rinv (lp x lp).
+constexpr int kTR = 2;                            // rows per register tile of the inverse
 __device__ void chol_inv_rows_tiled(float *R, int ld, float *S, int l, int lp, float *__restrict__ Rinv) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
@@ -170,45 +171,46 @@ __device__ void chol_inv_rows_tiled(float *R, int ld, float *S, int l, int lp, f
     for (int I = nb - 2; I >= 0; --I) {
         const int r0 = I * kNB, c0 = r0 + kNB;
         const int lds = ld - c0, wq = lds / 4;
-        // S[i][cc] = sum_{c0 <= t <= c} R[r0+i][t] X[t][c], c = c0 + cc
-        for (int q = tid; q < (kNB / 4) * wq; q += nt) {
+        // S[i][cc] = sum_{c0 <= t <= c} R[r0+i][t] X[t][c], c = c0 + cc, in kTR x 4 tiles
+        // (small tiles: more threads share the triangular work, which is latency-bound)
+        for (int q = tid; q < (kNB / kTR) * wq; q += nt) {
             const int iq = q / wq, cq = q - iq * wq;
-            const int i0 = r0 + 4 * iq, cc0 = 4 * cq;
-            float acc[4][4] = {};
+            const int i0 = r0 + kTR * iq, cc0 = 4 * cq;
+            float acc[kTR][4] = {};
             const int tend = c0 + cc0 + 4;
             for (int t = c0; t < tend; ++t) {
                 const float4 v = *reinterpret_cast<const float4 *>(R + t * ld + c0 + cc0);
                 const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < kTR; ++x) {
                     const float u = R[(i0 + x) * ld + t];
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(u, vv[y], acc[x][y]);
                 }
             }
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-                *reinterpret_cast<float4 *>(S + (4 * iq + x) * lds + cc0) =
+            for (int x = 0; x < kTR; ++x)
+                *reinterpret_cast<float4 *>(S + (kTR * iq + x) * lds + cc0) =
                     make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
         }
         __syncthreads();
         // X[r0+i][c] = -sum_{s >= i} X[r0+i][r0+s] S[s][c - c0]
-        for (int q = tid; q < (kNB / 4) * wq; q += nt) {
+        for (int q = tid; q < (kNB / kTR) * wq; q += nt) {
             const int iq = q / wq, cq = q - iq * wq;
-            const int i0 = 4 * iq, cc0 = 4 * cq;
-            float acc[4][4] = {};
+            const int i0 = kTR * iq, cc0 = 4 * cq;
+            float acc[kTR][4] = {};
             for (int sr = i0; sr < kNB; ++sr) {
                 const float4 v = *reinterpret_cast<const float4 *>(S + sr * lds + cc0);
                 const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < kTR; ++x) {
                     const float u = R[(r0 + i0 + x) * ld + r0 + sr];
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(u, vv[y], acc[x][y]);
                 }
             }
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < kTR; ++x)
                 *reinterpret_cast<float4 *>(R + (r0 + i0 + x) * ld + c0 + cc0) =
                     make_float4(-acc[x][0], -acc[x][1], -acc[x][2], -acc[x][3]);
         }
