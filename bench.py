@@ -1035,8 +1035,13 @@ def main():
     kernel_files = ["paper_1412_3510_gb300/csrc/gemm_simt.cu"]
     if csr:
         peak = pk["hbm_gbs"]
+        # besides the algorithmic bytes, every nonzero gathers one lp-wide row of the block
+        # operand (X for A X, Q for A^T Q): from L2 when the block fits it
+        lp_csr = -(-(l + 1) // 8) * 8
+        gather = 4.0 * w["nnz"] * lp_csr
         roof = {"bound": "hbm", "achieved": gbs_per_pass, "peak": peak, "unit": "GB/s", "frac": gbs_per_pass / peak,
-                "peak_source": pk["source"], "kernel": "spmm kernels (A and A^T passes)"}
+                "peak_source": pk["source"], "kernel": "spmm kernels (A and A^T passes)",
+                "gather_bytes_per_pass": gather, "gather_gbs": gather / (avg_pass_ms * 1e-3) / 1e9}
         key = "spmm_csr"
         kernel_files = ["paper_1412_3510_gb300/csrc/csr.cu"]
     elif args.precision == "fp32":
