@@ -299,43 +299,46 @@ template <int G>
 __device__ __forceinline__ void group_dot(const int32_t *__restrict__ idx, const float *__restrict__ val, int32_t p0,
                                           int32_t p1, int64_t cols, const float4 *__restrict__ X4, int nv, int sub,
                                           bool c0ok, bool c1ok, float4 &a0, float4 &a1) {
-    int32_t p = p0;
-    for (; p + 4 <= p1; p += 4) {
-        int32_t j[4];
-        float v[4];
+    // Software-pipelined: the next step's indices and values load while this step's
+    // block rows are gathered, so a step waits for one memory round trip, not two.
+    // Nonzeros are accumulated in order p0, p0 + 1, ... (as a plain loop would).
+    int32_t jn[4];
+    float vn[4];
+    auto fetch = [&](int32_t p) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            j[u] = __ldg(idx + p + u);
-            v[u] = __ldg(val + p + u);
-            if ((uint32_t)j[u] >= (uint32_t)cols) { j[u] = 0; v[u] = 0.f; }
+            const bool in = p + u < p1;
+            jn[u] = in ? __ldg(idx + p + u) : 0;
+            vn[u] = in ? __ldg(val + p + u) : 0.f;
+        }
+    };
+    if (p0 < p1) fetch(p0);
+    for (int32_t p = p0; p < p1; p += 4) {
+        const int cnt = min(4, p1 - p);
+        int32_t j[4];
+        float v[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = jn[u];
+            v[u] = vn[u];
+            ok[u] = u < cnt && (uint32_t)j[u] < (uint32_t)cols;
         }
         float4 x0[4], x1[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float4 *xr = X4 + (int64_t)j[u] * nv;
-            x0[u] = c0ok ? __ldg(xr + sub) : make_float4(0.f, 0.f, 0.f, 0.f);
-            x1[u] = c1ok ? __ldg(xr + sub + G) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *xr = X4 + (int64_t)(ok[u] ? j[u] : 0) * nv;
+            x0[u] = (ok[u] && c0ok) ? __ldg(xr + sub) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x1[u] = (ok[u] && c1ok) ? __ldg(xr + sub + G) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if (p + 4 < p1) fetch(p + 4);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
             a0.x = fmaf(v[u], x0[u].x, a0.x); a0.y = fmaf(v[u], x0[u].y, a0.y);
             a0.z = fmaf(v[u], x0[u].z, a0.z); a0.w = fmaf(v[u], x0[u].w, a0.w);
             a1.x = fmaf(v[u], x1[u].x, a1.x); a1.y = fmaf(v[u], x1[u].y, a1.y);
             a1.z = fmaf(v[u], x1[u].z, a1.z); a1.w = fmaf(v[u], x1[u].w, a1.w);
-        }
-    }
-    for (; p < p1; ++p) {
-        const int32_t jj = __ldg(idx + p);
-        if ((uint32_t)jj >= (uint32_t)cols) continue;
-        const float vv = __ldg(val + p);
-        const float4 *xr = X4 + (int64_t)jj * nv;
-        if (c0ok) {
-            const float4 x = __ldg(xr + sub);
-            a0.x = fmaf(vv, x.x, a0.x); a0.y = fmaf(vv, x.y, a0.y); a0.z = fmaf(vv, x.z, a0.z); a0.w = fmaf(vv, x.w, a0.w);
-        }
-        if (c1ok) {
-            const float4 x = __ldg(xr + sub + G);
-            a1.x = fmaf(vv, x.x, a1.x); a1.y = fmaf(vv, x.y, a1.y); a1.z = fmaf(vv, x.z, a1.z); a1.w = fmaf(vv, x.w, a1.w);
         }
     }
 }
@@ -449,9 +452,20 @@ spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, const int2 *__restri
         const int64_t r = rq.x;
         const int64_t c0 = first[r], c1 = min((int64_t)first[r + 1], max_chunks);
         for (int c = lane; c < lp; c += 32) {
-            float s = 0.f;
-            for (int64_t k = c0; k < c1; ++k) s += part[k * lp + c];
-            Y[r * lp + c] = s;
+            // four partial sums (chunk k into sum k mod 4), combined in a fixed order:
+            // four loads in flight instead of one for rows of hundreds of chunks
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int64_t k = c0;
+            for (; k + 4 <= c1; k += 4) {
+                s0 += part[k * lp + c];
+                s1 += part[(k + 1) * lp + c];
+                s2 += part[(k + 2) * lp + c];
+                s3 += part[(k + 3) * lp + c];
+            }
+            if (k < c1) s0 += part[k * lp + c];
+            if (k + 1 < c1) s1 += part[(k + 1) * lp + c];
+            if (k + 2 < c1) s2 += part[(k + 2) * lp + c];
+            Y[r * lp + c] = (s0 + s1) + (s2 + s3);
         }
     }
 }
