@@ -343,6 +343,70 @@ __device__ __forceinline__ void group_dot(const int32_t *__restrict__ idx, const
     }
 }
 
+// Light rows in order of degree bucket (0, 1, 2-3, 4-7, ..., 129-256 nonzeros), so that
+// the rows sharing a warp have lengths within a factor of two: with power-law degrees a
+// warp would otherwise run as long as the longest of its rows.  The order within a
+// bucket comes from atomics and varies, which changes nothing: every row's sum is its
+// own.  Heavy rows are left out (their chunks have their own kernels).
+constexpr int kBuckets = 10;
+constexpr int kBucketRows = 1024;             // rows per CTA of the bucket kernels
+
+__device__ __forceinline__ int light_bucket(const int32_t *__restrict__ ptr, int64_t r, int64_t nnz) {
+    const int32_t p0 = max(ptr[r], 0), p1 = (int32_t)min((int64_t)ptr[r + 1], nnz);
+    const int d = p1 - p0;
+    if (d > kHeavy) return -1;
+    return d <= 0 ? 0 : 32 - __clz(d);
+}
+
+// cnt[b] += number of light rows in bucket b (cnt zeroed by the caller)
+__global__ void __launch_bounds__(256) bucket_count_kernel(const int32_t *__restrict__ ptr, int64_t rows, int64_t nnz,
+                                                           int32_t *__restrict__ cnt) {
+    __shared__ int h[kBuckets];
+    if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * kBucketRows;
+    for (int e = threadIdx.x; e < kBucketRows; e += blockDim.x) {
+        const int64_t r = r0 + e;
+        if (r < rows) {
+            const int b = light_bucket(ptr, r, nnz);
+            if (b >= 0) atomicAdd(&h[b], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+// cnt -> exclusive offsets in cur[0..kBuckets-1], the number of light rows in cur[kBuckets]
+__global__ void bucket_scan_kernel(const int32_t *__restrict__ cnt, int32_t *__restrict__ cur) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t run = 0;
+        for (int b = 0; b < kBuckets; ++b) { cur[b] = run; run += cnt[b]; }
+        cur[kBuckets] = run;
+    }
+}
+
+// perm[cur[b]++ ...] = the light rows of bucket b (one global atomic per CTA and bucket)
+__global__ void __launch_bounds__(256) bucket_scatter_kernel(const int32_t *__restrict__ ptr, int64_t rows, int64_t nnz,
+                                                             int32_t *__restrict__ cur, int32_t *__restrict__ perm) {
+    __shared__ int h[kBuckets], base[kBuckets];
+    if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * kBucketRows;
+    int bk[kBucketRows / 256], rk[kBucketRows / 256];
+#pragma unroll
+    for (int u = 0; u < kBucketRows / 256; ++u) {
+        const int64_t r = r0 + threadIdx.x + 256 * u;
+        bk[u] = r < rows ? light_bucket(ptr, r, nnz) : -1;
+        rk[u] = bk[u] >= 0 ? atomicAdd(&h[bk[u]], 1) : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets) base[threadIdx.x] = h[threadIdx.x] ? atomicAdd(&cur[threadIdx.x], h[threadIdx.x]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kBucketRows / 256; ++u)
+        if (bk[u] >= 0) perm[base[bk[u]] + rk[u]] = (int32_t)(r0 + threadIdx.x + 256 * u);
+}
+
 // light rows with several rows per warp: a group of G lanes per row, every warp keeping
 // (32 / G) x 4 x 2 float4 gathers in flight.  Needs lp % 4 == 0 and lp <= 8 G; heavy
 // rows are skipped.
@@ -350,7 +414,8 @@ template <int G>
 __global__ void __launch_bounds__(256, 4)
 spmm_light_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                         const float *__restrict__ val, int64_t rows, int64_t cols, int64_t nnz,
-                        const float *__restrict__ X, int lp, float *__restrict__ Y) {
+                        const float *__restrict__ X, int lp, float *__restrict__ Y, const int32_t *__restrict__ perm,
+                        const int32_t *__restrict__ nlight) {
     constexpr int R = 32 / G;                  // rows per warp
     const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -358,11 +423,13 @@ spmm_light_group_kernel(const int32_t *__restrict__ ptr, const int32_t *__restri
     const int nv = lp >> 2;
     const bool c0ok = sub < nv, c1ok = sub + G < nv;
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
-    for (int64_t rb = wid * R; rb < rows; rb += nw * R) {
-        const int64_t r = rb + grp;
+    const int64_t nl = min((int64_t)*nlight, rows);
+    for (int64_t rb = wid * R; rb < nl; rb += nw * R) {
+        const int64_t q = rb + grp;
+        const int64_t r = q < nl ? (int64_t)perm[q] : rows;
         int32_t p0 = 0, p1 = 0;
         bool write = false;
-        if (r < rows) {
+        if (r >= 0 && r < rows) {
             p0 = max(ptr[r], 0);
             p1 = (int32_t)min((int64_t)ptr[r + 1], nnz);
             write = p1 - p0 <= kHeavy;
@@ -480,6 +547,8 @@ struct Spmm {
     const float *val = nullptr;
     int64_t rows = 0, cols = 0, nnz = 0, max_chunks = 0;
     int32_t *first = nullptr;      // rows + 1
+    int32_t *perm = nullptr;       // rows: light rows by degree bucket
+    int32_t *bk = nullptr;         // 2 kBuckets + 1: bucket counts, offsets / the number of light rows
     int2 *table = nullptr;         // max_chunks
     float *part = nullptr;         // max_chunks x max_lp
     int64_t *scan_tmp = nullptr;   // scan_tiles(rows + 1)
@@ -487,6 +556,15 @@ struct Spmm {
     int plan(cudaStream_t s) const {
         chunk_count_kernel<<<grid_for(rows + 1, 256), 256, 0, s>>>(ptr, rows, first);
         RPCA_CHECK_LAUNCH();
+        const int64_t bblocks = std::max<int64_t>(1, cdiv(rows, kBucketRows));
+        if (cudaMemsetAsync(bk, 0, (2 * kBuckets + 1) * sizeof(int32_t), s) != cudaSuccess) return RPCA_ERR_CUDA;
+        bucket_count_kernel<<<(unsigned)bblocks, 256, 0, s>>>(ptr, rows, nnz, bk);
+        RPCA_CHECK_LAUNCH();
+        bucket_scan_kernel<<<1, 32, 0, s>>>(bk, bk + kBuckets);
+        RPCA_CHECK_LAUNCH();
+        bucket_scatter_kernel<<<(unsigned)bblocks, 256, 0, s>>>(ptr, rows, nnz, bk + kBuckets, perm);
+        RPCA_CHECK_LAUNCH();
+        // bucket_scatter advanced the offsets by the counts: bk[2 kBuckets] still holds the total
         RPCA_TRY(launch_scan(first, rows + 1, scan_tmp, s));
         if (max_chunks > 0) {
             chunk_table_kernel<<<grid_for(rows, 256), 256, 0, s>>>(ptr, first, rows, table, max_chunks);
@@ -498,11 +576,11 @@ struct Spmm {
         const bool vec = lp % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
                          (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
         if (vec && lp <= 64) {
-            spmm_light_group_kernel<8><<<grid_for(rows * 8, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+            spmm_light_group_kernel<8><<<grid_for(rows * 8, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, perm, bk + 2 * kBuckets);
         } else if (vec && lp <= 128) {
-            spmm_light_group_kernel<16><<<grid_for(rows * 16, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+            spmm_light_group_kernel<16><<<grid_for(rows * 16, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, perm, bk + 2 * kBuckets);
         } else if (vec && lp <= 256) {
-            spmm_light_group_kernel<32><<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
+            spmm_light_group_kernel<32><<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y, perm, bk + 2 * kBuckets);
         } else {
             spmm_light_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(ptr, idx, val, rows, cols, nnz, X, lp, Y);
         }
@@ -538,7 +616,8 @@ int64_t max_chunks_for(int64_t nnz, int64_t rows) {
 
 struct CsrScratch {
     size_t row_of = 0, keys0 = 0, keys1 = 0, rows0 = 0, rows1 = 0, vals0 = 0, vals1 = 0, hist = 0, tptr = 0,
-           first_a = 0, first_t = 0, table_a = 0, table_t = 0, part_a = 0, part_t = 0, scan = 0, total = 0;
+           first_a = 0, first_t = 0, table_a = 0, table_t = 0, part_a = 0, part_t = 0, scan = 0, perm_a = 0,
+           perm_t = 0, bk_a = 0, bk_t = 0, total = 0;
 };
 
 CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
@@ -562,6 +641,10 @@ CsrScratch csr_scratch(int64_t m, int64_t n, int64_t nnz, int max_lp) {
     S.part_a = take((size_t)max_chunks_for(nnz, m) * max_lp * 4);
     S.part_t = take((size_t)max_chunks_for(nnz, n) * max_lp * 4);
     S.scan = take((size_t)scan_tiles(std::max({(int64_t)256 * nblocks, m + 1, n + 1})) * 8);
+    S.perm_a = take((size_t)m * 4);
+    S.perm_t = take((size_t)n * 4);
+    S.bk_a = take((size_t)(2 * kBuckets + 1) * 4);
+    S.bk_t = take((size_t)(2 * kBuckets + 1) * 4);
     S.total = off;
     return S;
 }
@@ -590,6 +673,7 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     op.a.rows = m; op.a.cols = n; op.a.nnz = nnz; op.a.max_chunks = max_chunks_for(nnz, m);
     op.a.first = I(S.first_a); op.a.table = reinterpret_cast<int2 *>(base + S.table_a); op.a.part = F(S.part_a);
     op.a.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
+    op.a.perm = I(S.perm_a); op.a.bk = I(S.bk_a);
 
     int32_t *keys[2] = {I(S.keys0), I(S.keys1)};
     int32_t *rws[2] = {I(S.rows0), I(S.rows1)};
@@ -623,6 +707,7 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     op.t.rows = n; op.t.cols = m; op.t.nnz = nnz; op.t.max_chunks = max_chunks_for(nnz, n);
     op.t.first = I(S.first_t); op.t.table = reinterpret_cast<int2 *>(base + S.table_t); op.t.part = F(S.part_t);
     op.t.scan_tmp = reinterpret_cast<int64_t *>(base + S.scan);
+    op.t.perm = I(S.perm_t); op.t.bk = I(S.bk_t);
     RPCA_TRY(op.a.plan(s));
     RPCA_TRY(op.t.plan(s));
     return RPCA_OK;

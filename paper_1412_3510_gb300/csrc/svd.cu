@@ -346,23 +346,35 @@ svd_finish_kernel(int l, int lp, int k, int kp, float *__restrict__ Wk, float *_
 }
 
 // Per column r < k: flip V[:, r] when its largest-|entry| (first on ties) is
-// negative; apply the same sign to Wk[:, r]; S[r] = sig[r].
-__global__ void __launch_bounds__(256)
+// negative; apply the same sign to Wk[:, r]; S[r] = sig[r].  One CTA per column; each
+// thread scans its rows eight at a time (eight strided loads in flight), in increasing
+// row order, so "strictly greater" keeps the first index as in a plain scan.
+constexpr int kSignThreads = 1024;
+
+__global__ void __launch_bounds__(kSignThreads)
 sign_fix_kernel(float *__restrict__ V, int64_t n, int64_t ldv, float *__restrict__ Wk, int lp, int kp,
                 const float *__restrict__ sig, float *__restrict__ S) {
     const int r = blockIdx.x;
-    __shared__ float sv[256];
-    __shared__ int64_t si[256];
+    const int nt = blockDim.x;
+    __shared__ float sv[kSignThreads];
+    __shared__ int64_t si[kSignThreads];
     float best = -1.f;
     int64_t bi = 0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const float a = fabsf(V[i * ldv + r]);
-        if (a > best) { best = a; bi = i; }      // strictly greater keeps the first index
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += 8 * (int64_t)nt) {
+        float a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = i0 + (int64_t)u * nt;
+            a[u] = i < n ? fabsf(V[i * ldv + r]) : -1.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (a[u] > best) { best = a[u]; bi = i0 + (int64_t)u * nt; }   // strictly greater keeps the first index
     }
     sv[threadIdx.x] = best;
     si[threadIdx.x] = bi;
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    for (int off = nt / 2; off > 0; off >>= 1) {
         if (threadIdx.x < off) {
             const float ob = sv[threadIdx.x + off];
             const int64_t oi = si[threadIdx.x + off];
@@ -376,8 +388,8 @@ sign_fix_kernel(float *__restrict__ V, int64_t n, int64_t ldv, float *__restrict
     const bool flip = n > 0 && V[si[0] * ldv + r] < 0.f;
     __syncthreads();
     if (flip) {
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[i * ldv + r] = -V[i * ldv + r];
-        for (int i = threadIdx.x; i < lp; i += blockDim.x) Wk[(size_t)i * kp + r] = -Wk[(size_t)i * kp + r];
+        for (int64_t i = threadIdx.x; i < n; i += nt) V[i * ldv + r] = -V[i * ldv + r];
+        for (int i = threadIdx.x; i < lp; i += nt) Wk[(size_t)i * kp + r] = -Wk[(size_t)i * kp + r];
     }
     if (threadIdx.x == 0) S[r] = sig[r];
 }
@@ -423,7 +435,7 @@ int launch_small_svd(const float *R, int l, int lp, int k, int kp, float *Wk, fl
 
 int launch_sign_fix(float *V, int64_t n, int64_t ldv, int k, float *Wk, int lp, int kp,
                     const float *sig, float *S, cudaStream_t s) {
-    sign_fix_kernel<<<k, 256, 0, s>>>(V, n, ldv, Wk, lp, kp, sig, S);
+    sign_fix_kernel<<<k, kSignThreads, 0, s>>>(V, n, ldv, Wk, lp, kp, sig, S);
     RPCA_CHECK_LAUNCH();
     return RPCA_OK;
 }

@@ -35,6 +35,9 @@ def _check(csr, k, l, its, raw, seed, **kw):
     if kk:
         assert subspace_dist(Ug[:, :kk], Uo[:, :kk]) < tol
         assert subspace_dist(Vg[:, :kk], Vo[:, :kk]) < tol
+    # sign rule: the largest-magnitude entry of every right vector is positive
+    piv = np.abs(Vg).argmax(axis=0)
+    assert np.all(Vg[piv, np.arange(k)] > 0)
     est = rp.rpca_resid_norm_csr(rp_, ci, va, csr.shape, U, Sg, V, raw=raw, iters=20, seed=3)
     ref = O.resid_power(csr, Ug.astype(np.float32), sg.astype(np.float32), Vg.astype(np.float32), raw=raw,
                         iters=20, seed=3)
@@ -63,6 +66,14 @@ def test_tall_powerlaw_csr_parity():
     csr = sp.csr_matrix((va, ci, rp_), shape=(400000, 3000))
     assert np.diff(csr.tocsc().indptr).max() > 256       # heavy rows of A^T exist
     _check(csr, 10, 30, 2, False, seed=5)
+
+
+def test_wide_csr_parity():
+    """n = 60000 columns: the sign rule scans right vectors longer than one pass of its
+    1024-thread CTA (eight strided loads per thread per step)."""
+    rp_, ci, va = S.powerlaw_csr(20000, 60000, 400000, exponent=2.1, rank=6, seed=17)
+    csr = sp.csr_matrix((va, ci, rp_), shape=(20000, 60000))
+    _check(csr, 6, 10, 2, True, seed=9)
 
 
 def test_heavy_rows_and_empty_rows():
