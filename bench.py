@@ -303,7 +303,7 @@ def oracle_sample(A_host, w, rows):
     import oracle
     sub = A_host[:rows]
     t = time.perf_counter()
-    oracle.rpca(sub, w["k"], w["l"], w["its"], raw=w["raw"], seed=1)
+    oracle.rpca(sub, w["k"], w["l"], w.get("its_at_bar", w["its"]), raw=w["raw"], seed=1)
     return time.perf_counter() - t
 
 
@@ -356,7 +356,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"],
-                   "its": w["its"], "raw": w["raw"], "format": w.get("kind", "dense")},
+                   "its": w.get("its_at_bar", w["its"]), "its_configured": w["its"], "raw": w["raw"], "format": w.get("kind", "dense")},
         "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
                          "sample": f"FP64 numpy/scipy oracle on the first {rows} of {w['m']} rows, time scaled by m"},
         "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -373,7 +373,7 @@ def run_reference_square(args, w):
     def once(ns):
         a = synth.e2_matrix_np(ns, w["seed"])
         t0 = time.perf_counter()
-        oracle.rpca(a, w["k"], w["l"], w["its"], raw=w["raw"], seed=1)
+        oracle.rpca(a, w["k"], w["l"], w.get("its_at_bar", w["its"]), raw=w["raw"], seed=1)
         return time.perf_counter() - t0
     t_probe = once(1000)
     per_step = args.ref_budget / max(args.steps + args.warmup, 1)
@@ -388,7 +388,7 @@ def run_reference_square(args, w):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_full * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"],
-                   "its": w["its"], "raw": w["raw"], "format": "dense"},
+                   "its": w.get("its_at_bar", w["its"]), "its_configured": w["its"], "raw": w["raw"], "format": "dense"},
         "cpu_baseline": {"value": value, "unit": "PCA/s", "cores": cores(), "kind": "oracle",
                          "sample": f"FP64 numpy oracle on a {ns} x {ns} matrix of the same law, time scaled by mn"},
         "e2e": {"value": value, "unit": "PCA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

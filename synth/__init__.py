@@ -325,7 +325,10 @@ WORKLOADS = {
     # name: (m, n, k, l, its, raw, spectrum builder, seed)
     "dense_2000x1000_k10": dict(m=2000, n=1000, k=10, l=12, its=2, raw=False,
                                 spectrum=lambda r: spectrum_exp20(r), seed=1235),
-    "dense_100000x2000_k100": dict(m=100000, n=2000, k=100, l=102, its=2, raw=False,
+    # its_at_bar: the smallest its whose PCA of this (seeded, fixed) matrix meets resid <=
+    # 1.1 sigma_{k+1}, as bench.py's accuracy search finds it on the GPU (resid / sigma_101 =
+    # 1.179, 1.124, 1.088 at its = 2, 3, 4); the host reference times the oracle at it too
+    "dense_100000x2000_k100": dict(m=100000, n=2000, k=100, l=102, its=2, raw=False, its_at_bar=4,
                                    spectrum=lambda r: spectrum_pow15(r, 1236), seed=1236),
     "dense_200000x20000_k200": dict(m=200000, n=20000, k=200, l=210, its=2, raw=False,
                                     spectrum=lambda r: spectrum_exp50(r), seed=1237),
@@ -335,8 +338,9 @@ WORKLOADS = {
                                   spectrum=lambda r: spectrum_pow15(r, 1236), seed=1238),
     # Section 7's importance-of-power-iterations matrix: n x n i.i.d. N(sqrt(30/n), 1), signs
     # flipped where i*j is odd; rank 4, l = k + 2, its swept over 0, 2, 4; A itself (raw)
+    # its_at_bar = 3: resid / sigma_5 = 1.79 at its = 2, 1.07 at its = 3
     "e2_gaussian_100000_k4": dict(kind="e2", m=100000, n=100000, k=4, l=6, its=2, raw=True, its_sweep=(0, 2, 4),
-                                  seed=1243),
+                                  its_at_bar=3, seed=1243),
     "e2_gaussian_20000_k4": dict(kind="e2", m=20000, n=20000, k=4, l=6, its=2, raw=True, its_sweep=(0, 2, 4),
                                  seed=1244),
     # sparse: power-law row/column degrees (exponent 2.1), N(0,1) values plus a planted
