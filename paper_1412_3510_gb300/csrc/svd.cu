@@ -162,8 +162,8 @@ jacobi_kernel(const float *__restrict__ R, int l, float2 *__restrict__ rot, int 
         if (__int_as_float(s_mu) < tol) { ++sweep; early = true; break; }
         __syncthreads();
     }
-    // sweep = number of logged sweeps (the last one made no rotation or only rotations
-    // below kQuadStop, or the cap was hit)
+    // sweep = number of logged sweeps (the last one made no rotation, or every rotation's
+    // predicted next measure was below tol, or the cap was hit)
     if (tid == 0) {
         *sweeps_out = sweep;
         st->jacobi_sweeps = sweep;
