@@ -504,35 +504,48 @@ spmm_heavy_kernel(const int32_t *__restrict__ ptr, const int32_t *__restrict__ i
     }
 }
 
-// heavy rows: Y[r] = sum of its chunk partials in chunk order; one warp per row,
-// found through the chunk table (the row's first chunk, q = 0)
-__global__ void __launch_bounds__(256)
+// heavy rows: Y[r] = sum of its chunk partials, one CTA per row (found through the chunk
+// table: the row's first chunk, q = 0).  Warp w sums chunks w, w + 8, ... with four
+// interleaved partial sums; the eight warp sums are added in warp order (a fixed tree,
+// so the result is deterministic).  A row of hundreds of chunks then has 32 loads in
+// flight per column instead of one warp walking them.
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(kReduceWarps * 32)
 spmm_heavy_reduce_kernel(const int32_t *__restrict__ first, const int2 *__restrict__ table, int64_t rows,
                          int64_t max_chunks, const float *__restrict__ part, int lp, float *__restrict__ Y) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ float ws[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nchunks = min((int64_t)first[rows], max_chunks);
-    for (int64_t ch = wid; ch < nchunks; ch += nw) {
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int2 rq = table[ch];
-        if (rq.y != 0) continue;
+        if (rq.y != 0) continue;                        // CTA-uniform
         const int64_t r = rq.x;
         const int64_t c0 = first[r], c1 = min((int64_t)first[r + 1], max_chunks);
-        for (int c = lane; c < lp; c += 32) {
-            // four partial sums (chunk k into sum k mod 4), combined in a fixed order:
-            // four loads in flight instead of one for rows of hundreds of chunks
+        for (int cb = 0; cb < lp; cb += 32) {
+            const int c = cb + lane;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int64_t k = c0;
-            for (; k + 4 <= c1; k += 4) {
-                s0 += part[k * lp + c];
-                s1 += part[(k + 1) * lp + c];
-                s2 += part[(k + 2) * lp + c];
-                s3 += part[(k + 3) * lp + c];
+            if (c < lp) {
+                int64_t k = c0 + warp;
+                for (; k + 3 * kReduceWarps < c1; k += 4 * kReduceWarps) {
+                    s0 += part[k * lp + c];
+                    s1 += part[(k + kReduceWarps) * lp + c];
+                    s2 += part[(k + 2 * kReduceWarps) * lp + c];
+                    s3 += part[(k + 3 * kReduceWarps) * lp + c];
+                }
+                if (k < c1) s0 += part[k * lp + c];
+                if (k + kReduceWarps < c1) s1 += part[(k + kReduceWarps) * lp + c];
+                if (k + 2 * kReduceWarps < c1) s2 += part[(k + 2 * kReduceWarps) * lp + c];
             }
-            if (k < c1) s0 += part[k * lp + c];
-            if (k + 1 < c1) s1 += part[(k + 1) * lp + c];
-            if (k + 2 < c1) s2 += part[(k + 2) * lp + c];
-            Y[r * lp + c] = (s0 + s1) + (s2 + s3);
+            ws[warp][lane] = (s0 + s1) + (s2 + s3);
+            __syncthreads();
+            if (warp == 0 && c < lp) {
+                float t = ws[0][lane];
+#pragma unroll
+                for (int w = 1; w < kReduceWarps; ++w) t += ws[w][lane];
+                Y[r * lp + c] = t;
+            }
+            __syncthreads();
         }
     }
 }
@@ -600,8 +613,8 @@ struct Spmm {
                                                                                 nnz, table, max_chunks, X, lp, part);
             }
             RPCA_CHECK_LAUNCH();
-            spmm_heavy_reduce_kernel<<<grid_for(max_chunks * 32, 256), 256, 0, s>>>(first, table, rows, max_chunks,
-                                                                                   part, lp, Y);
+            spmm_heavy_reduce_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(max_chunks, (int64_t)num_sms() * 8)),
+                                       kReduceWarps * 32, 0, s>>>(first, table, rows, max_chunks, part, lp, Y);
             RPCA_CHECK_LAUNCH();
         }
         return RPCA_OK;
