@@ -22,19 +22,18 @@ constexpr int kHeavy = 256;
 constexpr int kTile = 4096;            // radix sort: nonzeros per block (8 warps x 512)
 constexpr int kSortThreads = 256;
 
-__device__ __forceinline__ int64_t upper_bound_ptr(const int32_t *__restrict__ ptr, int64_t rows, int64_t p) {
-    // largest r in [0, rows) with ptr[r] <= p
-    int64_t lo = 0, hi = rows;                 // invariant: ptr[lo] <= p, answer in [lo, hi)
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)ptr[mid] <= p) lo = mid; else hi = mid;
+// row_of[p] = r for every nonzero p of row r: one warp per row, lanes across its range
+// (coalesced stores).  Ranges are clamped to [0, nnz); positions that no row covers (a
+// malformed row_ptr, reported by csr_check_kernel) keep the zero the caller wrote.
+__global__ void __launch_bounds__(256) row_expand_kernel(const int32_t *__restrict__ ptr, int64_t rows, int64_t nnz,
+                                                         int32_t *__restrict__ row_of) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = wid; r < rows; r += nw) {
+        const int64_t p0 = max((int64_t)ptr[r], (int64_t)0), p1 = min((int64_t)ptr[r + 1], nnz);
+        for (int64_t p = p0 + lane; p < p1; p += 32) row_of[p] = (int32_t)r;
     }
-    return lo;
-}
-
-__global__ void nnz_row_kernel(const int32_t *__restrict__ ptr, int64_t rows, int64_t nnz, int32_t *__restrict__ row_of) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        row_of[p] = (int32_t)upper_bound_ptr(ptr, rows, p);
 }
 
 __global__ void copy_i32_kernel(const int32_t *__restrict__ a, int32_t *__restrict__ b, int64_t n) {
@@ -695,7 +694,8 @@ int prepare(CsrOp &op, const int32_t *row_ptr, const int32_t *col_idx, const flo
     csr_check_kernel<<<grid_for(std::max(m, nnz), 256), 256, 0, s>>>(row_ptr, col_idx, m, n, nnz, st);
     RPCA_CHECK_LAUNCH();
     if (nnz > 0) {
-        nnz_row_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(row_ptr, m, nnz, rws[0]);
+        if (cudaMemsetAsync(rws[0], 0, (size_t)nnz * sizeof(int32_t), s) != cudaSuccess) return RPCA_ERR_CUDA;
+        row_expand_kernel<<<grid_for(m * 32, 256), 256, 0, s>>>(row_ptr, m, nnz, rws[0]);
         RPCA_CHECK_LAUNCH();
         copy_i32_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(col_idx, keys[0], nnz);
         RPCA_CHECK_LAUNCH();
