@@ -221,6 +221,29 @@ def traffic_from_profiles(kernel_key, sha):
     return None
 
 
+def split_bf16_roofline(m, n, l, pass_bytes, avg_pass_ms, pk):
+    """Roofline block of the split-BF16 passes over a dense m x n A.
+
+    The passes issue three BF16 products of width N = round_up(round_up(l + 1, 8), 16)
+    (a_hi b_hi, a_hi b_lo, a_lo b_hi): 6 m n N flops per pass on the tensor cores, and move
+    pass_bytes.  Whichever of the HBM time and the tensor time is larger bounds the pass; the
+    tensor peak is the sustained bf16 figure (the passes run inside a long step).  The other
+    fraction is reported beside the bound's."""
+    n_mma = -(-(l + 1) // 8) * 8
+    n_mma = -(-n_mma // 16) * 16
+    tc_flops = 6.0 * m * n * n_mma
+    tc_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+    gbs = pass_bytes / (avg_pass_ms * 1e-3) / 1e9
+    tflops = tc_flops / (avg_pass_ms * 1e-3) / 1e12
+    if tc_flops / (tc_peak * 1e12) > pass_bytes / (pk["hbm_gbs"] * 1e9):
+        return {"bound": "tensor", "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": tflops / tc_peak, "peak_source": pk["source"] + " (bf16, sustained)",
+                "kernel": "tcgen05 pass kernels (3 split-BF16 products, N = %d)" % n_mma,
+                "hbm_gbs_achieved": gbs, "hbm_frac": gbs / pk["hbm_gbs"]}
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "peak_source": pk["source"], "kernel": "tcgen05 pass kernels", "tensor_frac": tflops / tc_peak}
+
+
 def max_over_ranks(x, dist, world, device):
     """The largest of every rank's x (the slowest rank's time); x itself with one rank."""
     if world <= 1:
@@ -1052,27 +1075,7 @@ def main():
                 "kernel": "sgemm_kernel (A X and A^T Q passes)"}
         key = "sgemm_pass_fp32"
     else:
-        # The split-BF16 passes issue three BF16 products of width N = round_up(l + 1, 16)
-        # (a_hi b_hi, a_hi b_lo, a_lo b_hi): 6 m n N flops per pass on the tensor cores.
-        # Whichever of the HBM time and the tensor time is larger bounds the pass; the
-        # tensor peak is the sustained bf16 figure (the passes run inside a long step).
-        n_mma = -(-(l + 1) // 8) * 8
-        n_mma = -(-n_mma // 16) * 16
-        tc_flops = 6.0 * m * n * n_mma
-        tc_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
-        t_hbm = pass_bytes / (pk["hbm_gbs"] * 1e9)
-        t_tc = tc_flops / (tc_peak * 1e12)
-        if t_tc > t_hbm:
-            achieved = tc_flops / (avg_pass_ms * 1e-3) / 1e12
-            roof = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tc_peak, "peak_source": pk["source"] + " (bf16, sustained)",
-                    "kernel": "tcgen05 pass kernels (3 split-BF16 products, N = %d)" % n_mma,
-                    "hbm_gbs_achieved": gbs_per_pass, "hbm_frac": gbs_per_pass / pk["hbm_gbs"]}
-        else:
-            peak = pk["hbm_gbs"]
-            roof = {"bound": "hbm", "achieved": gbs_per_pass, "peak": peak, "unit": "GB/s",
-                    "frac": gbs_per_pass / peak, "peak_source": pk["source"], "kernel": "tcgen05 pass kernels",
-                    "tensor_frac": tc_flops / (avg_pass_ms * 1e-3) / 1e12 / tc_peak}
+        roof = split_bf16_roofline(m, n, l, pass_bytes, avg_pass_ms, pk)
         key = "tc_pass_bf16x3"
         kernel_files = ["paper_1412_3510_gb300/csrc/tc_gemm.cu", "paper_1412_3510_gb300/csrc/tc_ptx.cuh"]
     sha = source_sha(kernel_files)

@@ -20,3 +20,21 @@ def test_sigma_k1_secular_matches_svd_of_centred_matrix():
     for k in (0, 5, 17, n - 3):
         got = bench.sigma_k1_secular(sigma, U.sum(0), m, k)
         assert abs(got - s[k]) <= 1e-10 * s[0], (k, got, s[k])
+
+
+def test_split_bf16_roofline_bound():
+    """HBM-bound at l = 102 (N = 112), tensor-bound at l = 210 (N = 224) on the measured peaks;
+    fractions from the pass time by the stated formulas."""
+    pk = {"hbm_gbs": 6748.0, "bf16_tflops": 1925.8, "bf16_tflops_sustained": 1725.8, "source": "measured"}
+    m, n, l = 100000, 2000, 102
+    pb = 4.0 * m * n + 4.0 * (m + n) * l
+    r = bench.split_bf16_roofline(m, n, l, pb, 0.165, pk)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - pb / 0.165e-3 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["tensor_frac"] - 6.0 * m * n * 112 / 0.165e-3 / 1e12 / 1725.8) < 1e-9
+    m, n, l = 200000, 20000, 210
+    pb = 4.0 * m * n + 4.0 * (m + n) * l
+    r = bench.split_bf16_roofline(m, n, l, pb, 5.0, pk)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 6.0 * m * n * 224 / 5e-3 / 1e12) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 1725.8) < 1e-12
