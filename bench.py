@@ -209,14 +209,16 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_key, sha):
+def traffic_from_profiles(kernel_key, sha, workload=None):
+    """DRAM bytes per launch from profiles/traffic.json: only for the same kernel source
+    (sha) and, where the entry names one, the same workload; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel_key)
-    if e and e.get("src_sha") == sha:
+    if e and e.get("src_sha") == sha and (e.get("workload") is None or e.get("workload") == workload):
         return e.get("traffic_bytes_per_launch")
     return None
 
@@ -1079,7 +1081,7 @@ def main():
         key = "tc_pass_bf16x3"
         kernel_files = ["paper_1412_3510_gb300/csrc/tc_gemm.cu", "paper_1412_3510_gb300/csrc/tc_ptx.cuh"]
     sha = source_sha(kernel_files)
-    roof["traffic"] = traffic_from_profiles(key, sha)
+    roof["traffic"] = traffic_from_profiles(key, sha, args.workload)
 
     # end to end through the public API with host buffers
     e2e = None
