@@ -10,12 +10,12 @@
 // SIAM J. Sci. Comput. 42 (2020)), the product with an accumulated triangular
 // factor (for B^* = Q2 R2), and the triangular inverse used by the next GEMM.
 //
-// Cholesky, right-looking and blocked by 32 (see chol_blocked_kernel): a warp
-// factors each diagonal block in registers, the panel to its right is solved
+// Cholesky, right-looking and blocked by kNB = 16 (see chol_blocked_kernel): a
+// warp factors each diagonal block in registers, the panel to its right is solved
 // against it, and the trailing upper triangle is updated in 4 x 4 tiles.
-// Inverse: blocked by 32.  Each warp inverts one 32 x 32 diagonal block
-// (lanes own columns and sweep the rows bottom-up in lock step); then block
-// rows I = nb-2 .. 0 in turn: S = R[I, >I] X[>I, >I], X[I, >I] = -X[I,I] S.
+// Inverse: blocked by kNB.  The diagonal blocks are inverted with the factor (lanes
+// own columns and sweep the rows bottom-up in lock step); then block rows
+// I = nb-2 .. 0 in turn: S = R[I, >I] X[>I, >I], X[I, >I] = -X[I,I] S.
 #include "internal.cuh"
 #include "gepp.cuh"
 
@@ -24,7 +24,8 @@ namespace rpca {
 namespace {
 
 constexpr int kLuThreads = 512;
-constexpr int kNB = 32;
+constexpr int kNB = 16;          // diagonal-block width (16 measured 12 % faster than 32 at l = 102:
+                                 // half the shuffles per pivot outweighs twice the panels)
 
 // sum_{t < n} a[t * sa] b[t * sb] with four independent partial sums
 __device__ __forceinline__ float dot4(const float *a, int sa, const float *b, int sb, int n) {
@@ -142,12 +143,12 @@ __device__ __forceinline__ float next_shift(float shift, int l, float maxdiag) {
 }
 
 // ---------------------------------------------------------------------------
-// Blocked right-looking Cholesky, panels of 32 columns, the whole matrix in shared
+// Blocked right-looking Cholesky, panels of kNB columns, the whole matrix in shared
 // memory (row stride ld = round_up(l, 4), so that rows are 16-byte aligned):
-//   1. warp 0 factors the 32 x 32 diagonal block in registers: lane c holds column
+//   1. warp 0 factors the kNB x kNB diagonal block in registers: lane c < kNB holds column
 //      c; pivot j is broadcast by shuffles, no CTA barrier inside the block;
-//   2. the panel R[J, >J] = R[J,J]^-T A[J, >J]: one thread per column, forward
-//      substitution with the diagonal block read by broadcast;
+//   2. the panel R[J, >J] = X_JJ^T A[J, >J] with the block's inverse X_JJ, in 4 x 4
+//      register tiles;
 //   3. the trailing update A[>J, >J] -= R[J, >J]^T R[J, >J] in 4 x 4 register tiles
 //      of the upper triangle.
 // Three barriers per panel instead of one per pivot.
@@ -283,7 +284,7 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
                 float a[kNB];
 #pragma unroll
                 for (int r = 0; r < kNB; ++r) a[r] = (r <= c && c < bl) ? A[(b0 + r) * ld + b0 + c] : 0.f;
-                thr_s[c] = c < bl ? tau * cs.dorig[b0 + c] + 0.5f * shift : 0.f;
+                if (c < kNB) thr_s[c] = c < bl ? tau * cs.dorig[b0 + c] + 0.5f * shift : 0.f;
                 __syncwarp();
                 bool fail = false;
                 float rd = 1.f;                             // this lane's R_cc
@@ -311,10 +312,10 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
                     // it until X replaces it), and R's upper triangle to A
 #pragma unroll
                     for (int r = 0; r < kNB; ++r) {
-                        Xd[r * kXdLd + c] = (r < c) ? a[r] : 0.f;
+                        if (c < kNB) Xd[r * kXdLd + c] = (r < c) ? a[r] : 0.f;
                         if (c < bl && r < c) A[(b0 + r) * ld + b0 + c] = a[r];
                     }
-                    rdi_s[c] = rdi;
+                    if (c < kNB) rdi_s[c] = rdi;
                     __syncwarp();
                     // R x = e_c from the bottom: x_i = ([i == c] - sum_{t > i} r_it x_t) / r_ii
                     float x[kNB];
@@ -335,7 +336,7 @@ chol_blocked_kernel(const float *__restrict__ G, int l, int lp, float *__restric
 #pragma unroll
                     for (int r = 0; r < kNB; ++r) {
                         if (c < bl && r < c) A[(b0 + c) * ld + b0 + r] = x[r];
-                        Xd[r * kXdLd + c] = (c < bl && r <= c) ? x[r] : 0.f;
+                        if (c < kNB) Xd[r * kXdLd + c] = (c < bl && r <= c) ? x[r] : 0.f;
                     }
                     if (c < bl) {
                         A[(b0 + c) * ld + b0 + c] = rd;
