@@ -38,3 +38,18 @@ def test_split_bf16_roofline_bound():
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - 6.0 * m * n * 224 / 5e-3 / 1e12) < 1e-6 * r["achieved"]
     assert abs(r["frac"] - r["achieved"] / 1725.8) < 1e-12
+
+
+def test_traffic_only_for_the_captured_kernel_and_workload(tmp_path, monkeypatch):
+    """profiles/traffic.json entries apply to one kernel source (hash) and one workload."""
+    import json
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"k": {"src_sha": "abc", "traffic_bytes_per_launch": 5.0, "workload": "w1"},
+         "k2": {"src_sha": "def", "traffic_bytes_per_launch": 7.0}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("k", "abc", "w1") == 5.0
+    assert bench.traffic_from_profiles("k", "abc", "w2") is None      # another workload
+    assert bench.traffic_from_profiles("k", "xyz", "w1") is None      # the kernel changed
+    assert bench.traffic_from_profiles("k2", "def", "any") == 7.0     # no workload named
+    assert bench.traffic_from_profiles("missing", "abc", "w1") is None
